@@ -1,0 +1,323 @@
+"""Pins for the FP64 CPU oracle, against what the paper and the mathematics fix.
+
+None of these re-types the oracle's own cascade: they check closed forms,
+invariants, an independent algorithm (Gauss-Seidel sweeping, Sec. 2.2),
+the paper's own algorithm run point by point (Algorithm 2), residuals of
+eq. (6) written in its "^+" form, refinement toward the Euclidean distance,
+and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_15869_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+# ---------------------------------------------------------------- local solve
+def test_local_solve_golden_closed_forms():
+    """Alg 1.1 / 1.3 roots of eq. (4)/(6) on a unit grid (tests/golden/local_solve.txt)."""
+    rows = _golden_rows("local_solve.txt")
+    assert len(rows) >= 10
+    for ax, ay, az, tau, want in rows:
+        got = oracle.local_solve(ax, ay, az, tau)
+        if math.isinf(want):
+            assert math.isinf(got) and got > 0
+        else:
+            assert got == pytest.approx(want, rel=4e-16, abs=0), (ax, ay, az, tau)
+
+
+def _plus_residual(u, a, tau):
+    return sum(max(u - v, 0.0) ** 2 for v in a if math.isfinite(v)) - tau * tau
+
+
+def test_local_solve_satisfies_eq6_and_is_upwind():
+    """The root solves sum ((u - a_d)^+)^2 = tau^2 and lies in [a1 + tau/sqrt(3), a1 + tau]."""
+    rng = np.random.default_rng(0)
+    for _ in range(20000):
+        a = list(rng.uniform(0, 3, size=3))
+        k = rng.integers(0, 4)
+        for q in range(k):
+            a[q] = math.inf
+        tau = float(rng.uniform(0.01, 2.0))
+        u = oracle.local_solve(*a, tau)
+        fin = [v for v in a if math.isfinite(v)]
+        if not fin:
+            assert math.isinf(u)
+            continue
+        a1 = min(fin)
+        assert a1 + tau / math.sqrt(3) - 1e-12 <= u <= a1 + tau + 1e-12
+        assert abs(_plus_residual(u, a, tau)) <= 1e-12 * max(1.0, tau * tau)
+
+
+def test_local_solve_symmetry_shift_and_scale():
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        a = rng.uniform(0, 1, size=3)
+        tau = float(rng.uniform(0.05, 1.0))
+        u = oracle.local_solve(*a, tau)
+        for perm in ([1, 0, 2], [2, 1, 0], [1, 2, 0]):
+            assert oracle.local_solve(*a[perm], tau) == pytest.approx(u, rel=1e-14)
+        assert oracle.local_solve(*(a + 5.0), tau) == pytest.approx(u + 5.0, rel=1e-13)
+        assert oracle.local_solve(*(3.0 * a), 3.0 * tau) == pytest.approx(3.0 * u, rel=1e-13)
+
+
+def test_local_solve_monotone_in_neighbours():
+    """Godunov scheme monotonicity: raising a neighbour minimum never lowers u."""
+    rng = np.random.default_rng(2)
+    for _ in range(5000):
+        a = rng.uniform(0, 1, size=3)
+        tau = float(rng.uniform(0.05, 1.0))
+        u = oracle.local_solve(*a, tau)
+        b = a.copy()
+        b[rng.integers(0, 3)] += float(rng.uniform(0, 0.5))
+        assert oracle.local_solve(*b, tau) >= u - 1e-15
+
+
+# ---------------------------------------------------------------- FMM vs GS vs Alg 2
+@pytest.mark.parametrize("seed", range(40))
+def test_fmm_equals_gauss_seidel_and_algorithm2(seed):
+    """P5/P7: fast marching, alternating-sweep Gauss-Seidel (Sec. 2.2) and
+    Algorithm 2 reach the same discrete solution (Sec. 4.1: "all methods
+    produce exactly the same" solution)."""
+    inst = W.random_small(seed, max_edge=12, p_barrier=0.1 if seed % 3 == 0 else 0.0)
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+    gs, rounds = oracle.gs(inst.F, inst.h, inst.src_idx, inst.src_val)
+    ifim, st = oracle.ifim(inst.F, inst.h, inst.src_idx, inst.src_val)
+    fin = np.isfinite(phi)
+    assert np.array_equal(fin, np.isfinite(gs)) and np.array_equal(fin, np.isfinite(ifim))
+    scale = max(1.0, float(np.max(np.abs(phi[fin]))) if fin.any() else 1.0)
+    assert np.max(np.abs(phi[fin] - gs[fin]), initial=0) <= 1e-13 * scale
+    assert np.max(np.abs(phi[fin] - ifim[fin]), initial=0) <= 1e-13 * scale
+
+
+def test_fmm_equals_gs_on_odd_shapes():
+    for dims in [(1, 1, 1), (7, 1, 1), (1, 9, 1), (1, 1, 6), (13, 7, 5), (5, 13, 7), (3, 3, 17)]:
+        inst = W.random_small(123, dims=dims, three_d=True)
+        phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+        gs, _ = oracle.gs(inst.F, inst.h, inst.src_idx, inst.src_val)
+        assert np.allclose(phi, gs, rtol=1e-13, atol=0), dims
+
+
+# ---------------------------------------------------------------- residual, causality
+@pytest.mark.parametrize("seed", range(10))
+def test_residual_zero_and_causality(seed):
+    """P3/P4: eq. (6) holds at every reachable non-source node; every such node
+    has an upwind neighbour lower by between tau/sqrt(d) and tau."""
+    inst = W.random_small(1000 + seed, max_edge=20, p_barrier=0.05)
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+    assert oracle.residual(inst.F, inst.h, inst.src_idx, phi) <= 1e-12
+    nx, ny, nz = inst.dims
+    P = phi.reshape(nz, ny, nx)
+    F = inst.F.reshape(nz, ny, nx)
+    pad = np.pad(P, 1, constant_values=np.inf)
+    nbmin = np.minimum.reduce([pad[:-2, 1:-1, 1:-1], pad[2:, 1:-1, 1:-1], pad[1:-1, :-2, 1:-1],
+                               pad[1:-1, 2:, 1:-1], pad[1:-1, 1:-1, :-2], pad[1:-1, 1:-1, 2:]])
+    src = np.zeros(P.size, bool)
+    src[inst.src_idx] = True
+    src = src.reshape(P.shape)
+    m = np.isfinite(P) & ~src
+    tau = inst.h / F[m]
+    d = 3 if nz > 1 else 2
+    gap = P[m] - nbmin[m]
+    assert np.all(gap <= tau * (1 + 1e-12))
+    assert np.all(gap >= tau / math.sqrt(d) * (1 - 1e-12))
+    assert np.all(P[np.isfinite(P)] >= inst.src_val.min() - 1e-15)
+
+
+def test_fmm_acceptance_order_is_monotone():
+    inst = W.random_small(77, dims=(11, 9, 8), three_d=True)
+    inst.src_val[:] = 0.0
+    phi, order = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val, return_order=True)
+    vals = phi.reshape(-1)[order]
+    assert np.all(np.diff(vals) >= 0)
+    assert order.size == np.isfinite(phi).sum()
+
+
+# ---------------------------------------------------------------- exactness along axes
+def test_axis_exactness_point_source_128():
+    """P2: F = 1, point source: phi along the grid lines through the source is k h."""
+    inst = W.point_source_2d(128, (64, 64))
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx)
+    k = np.arange(64)
+    assert np.allclose(phi[64, 64:128], k * inst.h, rtol=1e-14, atol=0)
+    assert np.allclose(phi[64, 64::-1], np.arange(65) * inst.h, rtol=1e-14, atol=0)
+    assert np.allclose(phi[64:128, 64], k * inst.h, rtol=1e-14, atol=0)
+    # symmetry of the constant-speed point-source solution
+    assert np.array_equal(phi[64 - 10:64 + 11, 64 - 10:64 + 11], phi[64 - 10:64 + 11, 64 - 10:64 + 11].T)
+
+
+def test_one_dimensional_sum_of_travel_times():
+    """A 1D grid is always one-sided: phi_k = sum_{j<=k} h / F_j exactly."""
+    rng = np.random.default_rng(5)
+    F = rng.uniform(0.2, 3.0, size=50)
+    phi = oracle.fmm(F.reshape(1, 50), 0.1, [0])
+    want = np.concatenate([[0.0], np.cumsum(0.1 / F[1:])])
+    assert np.allclose(phi[0], want, rtol=1e-14, atol=0)
+    # the same line embedded in 3D, with a slab of different speed
+    F3 = np.ones((5, 5, 40))
+    F3[:, :, 10:20] = 0.25
+    phi3 = oracle.fmm(F3, 0.5, [(2 * 5 + 2) * 40 + 0])
+    line = phi3[2, 2]
+    want3 = np.concatenate([[0.0], np.cumsum(0.5 / F3[2, 2, 1:])])
+    assert np.allclose(line, want3, rtol=1e-14, atol=0)
+
+
+def test_barriers_and_unreachable():
+    F = np.ones((9, 9))
+    F[:, 4] = 0.0                      # full wall
+    phi = oracle.fmm(F, 1.0, [0])
+    assert np.all(np.isinf(phi[:, 4:]))
+    assert np.all(np.isfinite(phi[:, :4]))
+    F[0, 4] = 1.0                      # a hole at the top
+    phi = oracle.fmm(F, 1.0, [0])
+    assert np.all(np.isinf(phi[1:, 4])) and np.isfinite(phi[0, 4])
+    assert np.all(np.isfinite(phi[:, 5:]))
+
+
+def test_duplicate_sources_keep_smaller_value_and_arg_errors():
+    F = np.ones((5, 5))
+    phi = oracle.fmm(F, 1.0, [12, 12], [0.7, 0.2])
+    assert phi[2, 2] == 0.2
+    with pytest.raises(ValueError):
+        oracle.fmm(np.full((3, 3), np.nan), 1.0, [0])
+    with pytest.raises(ValueError):
+        oracle.fmm(-np.ones((3, 3)), 1.0, [0])
+    with pytest.raises(ValueError):
+        oracle.fmm(F, 0.0, [0])
+    with pytest.raises(ValueError):
+        oracle.fmm(F, 1.0, [25])
+
+
+# ---------------------------------------------------------------- refinement
+def test_first_order_refinement_toward_euclidean_distance():
+    """P6: with F = 1 and a disc source initialised exactly, the max error
+    against |x| - R falls about 2x per halving of h (first-order scheme)."""
+    errs = []
+    R = 0.3
+    for n in (41, 81, 161, 321):
+        xs = np.linspace(-1, 1, n)
+        X, Y = np.meshgrid(xs, xs)
+        d = np.hypot(X, Y)
+        h = xs[1] - xs[0]
+        sel = d <= R + h
+        idx = np.flatnonzero(sel.reshape(-1))
+        val = np.maximum(d.reshape(-1)[idx] - R, 0.0)
+        phi = oracle.fmm(np.ones((n, n)), h, idx, val)
+        errs.append(np.max(np.abs(phi - np.maximum(d - R, 0.0))))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.6 < r < 2.6 for r in ratios), (errs, ratios)
+
+
+def test_point_source_refinement_rate():
+    """Point source: the error is O(h log 1/h) (the point singularity costs the
+    log factor), so err / (h ln(1/h)) stays within a narrow band while h halves
+    three times and the log-log slope is near 1 - 1/ln(1/h)."""
+    errs, hs = [], []
+    for n in (33, 65, 129, 257):
+        c = n // 2
+        inst = W.point_source_2d(n, (c, c))
+        phi = oracle.fmm(inst.F, inst.h, inst.src_idx)
+        xs = (np.arange(n) - c) * inst.h
+        X, Y = np.meshgrid(xs, xs)
+        errs.append(np.max(np.abs(phi - np.hypot(X, Y))))
+        hs.append(inst.h)
+    hs, errs = np.array(hs), np.array(errs)
+    c = errs / (hs * np.log(1.0 / hs))
+    assert np.all(np.diff(errs) < 0)
+    assert c.max() / c.min() < 1.25, (errs, c)
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert 0.65 <= slope <= 1.05, (errs, slope)
+
+
+# ---------------------------------------------------------------- Algorithm 2 behaviour
+def test_remedy_needed_only_where_the_paper_says():
+    """Sec. 4.2: Example 1 needs no remedy (Fig. 13); Examples 2 and 5 do
+    (Figs. 14-15).  Without Step 3 their Step-2 result differs from the
+    solution; with it, Algorithm 2 reaches the fast-marching solution."""
+    for ex, needs in ((1, False), (2, True), (5, True)):
+        inst = W.paper_example_2d(ex, n=101)
+        ref = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+        upd, st0 = oracle.ifim(inst.F, inst.h, inst.src_idx, inst.src_val, skip_remedy=True)
+        full, st = oracle.ifim(inst.F, inst.h, inst.src_idx, inst.src_val)
+        scale = np.max(ref[np.isfinite(ref)])
+        assert np.max(np.abs(full - ref)) <= 1e-12 * scale
+        err_upd = np.max(np.abs(upd - ref))
+        if needs:
+            assert st["remedy_seed"] > 0 and err_upd > 1e-6 * scale, (ex, st, err_upd)
+        else:
+            assert st["remedy_seed"] == 0 and err_upd == 0.0, (ex, st, err_upd)
+        # Step-2 values are upper bounds of the solution (phi only decreases)
+        assert np.all(upd >= ref - 1e-12 * scale)
+
+
+# ---------------------------------------------------------------- adjoint
+def test_adjoint_1d_exact():
+    """P8: on a 1D line, d phi_n / d s_k = h for every k in 1..n."""
+    n = 30
+    F = np.linspace(0.5, 2.0, n).reshape(1, n)
+    h = 0.2
+    phi = oracle.fmm(F, h, [0])
+    r = np.zeros_like(phi)
+    r[0, n - 1] = 1.0
+    g = oracle.adjoint(F, h, [0], phi, r)
+    assert g[0, 0] == 0.0
+    assert np.allclose(g[0, 1:], h, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adjoint_homogeneity_identity(seed):
+    """phi(c s) = c phi(s) with zero-valued sources, so sum_i s_i dL/ds_i = sum_rec r phi_rec."""
+    inst = W.random_small(500 + seed, max_edge=14, three_d=True)
+    inst.src_val[:] = 0.0
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+    rng = np.random.default_rng(seed)
+    r = np.where(np.isfinite(phi), rng.standard_normal(phi.shape), 0.0)
+    g = oracle.adjoint(inst.F, inst.h, inst.src_idx, phi, r)
+    s = 1.0 / inst.F
+    lhs = float(np.sum(s * g))
+    rhs = float(np.sum(np.where(np.isfinite(phi), r * phi, 0.0)))
+    assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adjoint_matches_central_finite_differences(seed):
+    """Adjoint vs central differences of the fast-marching solve, in FP64."""
+    inst = W.random_small(900 + seed, dims=(9, 8, 7), three_d=True, f_lo=0.5, f_hi=2.0)
+    inst.src_val[:] = 0.0
+    rng = np.random.default_rng(seed)
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx)
+    rec = rng.choice(phi.size, size=6, replace=False)
+    target = phi.reshape(-1)[rec] * (1 + 0.1 * rng.standard_normal(6))
+
+    def loss(F):
+        p = oracle.fmm(F, inst.h, inst.src_idx).reshape(-1)
+        return 0.5 * np.sum((p[rec] - target) ** 2)
+
+    r = np.zeros(phi.size)
+    r[rec] = phi.reshape(-1)[rec] - target
+    g = oracle.adjoint(inst.F, inst.h, inst.src_idx, phi, r.reshape(phi.shape)).reshape(-1)
+    s = (1.0 / inst.F).reshape(-1)
+    cells = rng.choice(phi.size, size=12, replace=False)
+    eps = 1e-6
+    fd = []
+    for c in cells:
+        sp = s.copy(); sp[c] += eps
+        sm = s.copy(); sm[c] -= eps
+        fd.append((loss((1 / sp).reshape(phi.shape)) - loss((1 / sm).reshape(phi.shape))) / (2 * eps))
+    fd = np.array(fd)
+    assert np.linalg.norm(g[cells] - fd) <= 1e-5 * max(np.linalg.norm(fd), 1e-12)
