@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the improved-FIM Eikonal solve on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload oscillating_256|point_source_128|maze_512|lognormal_batch64]
+
+One step = one complete solve (Steps 1-3 of Algorithm 2 and the output
+unpack) of the workload, inputs already resident in HBM.  The metric is
+converged grid nodes per second, FP32.  Each step's device time is measured
+with CUDA events on the solve's stream (first to last kernel); L2 is flushed
+between steps by a 256 MiB write outside the measured interval.  With N > 1
+(torchrun) every rank solves its own replica (weak scaling, no collective on
+the data path); value = nodes over all ranks / max over ranks of the time.
+
+--impl reference times the FP64 CPU oracle (fast marching) on the host cores
+on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged grid nodes/sec and % HBM roofline, FP32 at 1e-4 rel; fwd+adjoint vs plain"
+UNIT = "nodes/s"
+# algorithmic bytes per node of the Step-2/3 loop kernel (FP32): every node is
+# read (phi, tau) and written (phi) at least once in Step 2, and read (phi,
+# tau) once by the Step-3 recomputation: 12 + 8 = 20 B.
+LOOP_BYTES_PER_NODE = 20
+# whole step incl. layout conversion: F read, tau/phi brick writes (12 B),
+# the loop (20 B), unpack read + write (8 B)
+STEP_BYTES_PER_NODE = 40
+FALLBACK_HBM_GBS = 6400.0
+
+# DRAM traffic of one k_persistent launch on the default workload, from an
+# ncu capture (profiles/); valid only while the kernel sources hash matches.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_15869_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name: str):
+    from paper_2106_15869_b300 import workloads as W
+    if name == "oscillating_256":
+        return [W.oscillating_3d(256)]
+    if name == "point_source_128":
+        return [W.point_source_2d(128, (64, 64))]
+    if name == "maze_512":
+        return [W.maze_3d(512)]
+    if name == "lognormal_batch64":
+        return W.lognormal_batch(64)
+    raise ValueError(name)
+
+
+def cpu_sample(name: str):
+    """Bounded sample of the workload for the oracle timing."""
+    from paper_2106_15869_b300 import workloads as W
+    if name == "oscillating_256":
+        return W.oscillating_3d(256), "full 256^3 oscillating-speed grid, one FMM solve"
+    if name == "point_source_128":
+        return W.point_source_2d(128, (64, 64)), "full 128^2 grid"
+    if name == "maze_512":
+        return W.maze_3d(192, n_slabs=6, gap=12), "192^3 maze built by the same recipe (6 slabs/axis)"
+    return W.lognormal_batch(4)[0], "first instance of the lognormal batch"
+
+
+def run_reference(args, ws, rank):
+    import numpy as np
+    import oracle
+    if rank != 0:
+        return 0
+    inst, desc = cpu_sample(args.workload)
+    F = inst.F.astype(np.float32).astype(np.float64)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.fmm(F, inst.h, inst.src_idx, inst.src_val)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = inst.n_nodes * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": desc, "nodes_per_step": inst.n_nodes},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2106_15869_b300 import api, _lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    insts = make_workload(args.workload)
+    n_nodes = sum(i.n_nodes for i in insts)
+    wsp = api.Workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    if len(insts) == 1:
+        inst = insts[0]
+        F = torch.as_tensor(inst.F, dtype=torch.float32).to(dev)
+        idx = torch.as_tensor(inst.src_idx).to(dev)
+        val = torch.as_tensor(inst.src_val, dtype=torch.float32).to(dev)
+        phi = torch.empty_like(F)
+
+        def step(stats=True):
+            return api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp,
+                             out=phi, return_stats=stats, order=args.order)
+    else:
+        probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h, i.src_val) for i in insts]
+
+        def step(stats=True):
+            return api.solve_batched(probs, tile=args.tile, schedule=args.schedule, workspace=wsp,
+                                     return_stats=stats, order=args.order)
+
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    for _ in range(args.warmup):
+        _, st = step()
+        if st["status"] != 0:
+            raise RuntimeError(f"solve failed: {st}")
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    tot, loop, stats = [], [], []
+    for _ in range(args.steps):
+        flush_buf.zero_()
+        _, st = step()
+        tot.append(st["ms_total"])
+        loop.append(st["ms_loop"])
+        stats.append(st)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    total_s = sum(tot) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = n_nodes * args.steps * ws / total_s
+    ms_step = 1e3 * total_s / args.steps
+    loop_ms = statistics.mean(loop)
+
+    # end to end through the public API: pinned host F in, host phi out, every step
+    e2e = None
+    if len(insts) == 1:
+        F_h = torch.as_tensor(inst.F, dtype=torch.float32).pin_memory()
+        phi_h = torch.empty_like(F_h).pin_memory()
+        idx_h = torch.as_tensor(inst.src_idx).pin_memory()
+        val_h = torch.as_tensor(inst.src_val, dtype=torch.float32).pin_memory()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_ms = []
+        for s in range(args.steps + 1):
+            flush_buf.zero_()
+            ev0.record(stream)
+            F.copy_(F_h, non_blocking=True)
+            idx.copy_(idx_h, non_blocking=True)
+            val.copy_(val_h, non_blocking=True)
+            api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp, out=phi,
+                      order=args.order)
+            phi_h.copy_(phi, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            if s > 0:
+                e2e_ms.append(ev0.elapsed_time(ev1))
+        h2d = F_h.numel() * 4 + idx_h.numel() * 8 + val_h.numel() * 4
+        e2e = {"value": n_nodes * ws / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(phi_h.numel() * 4),
+               "ms_per_step": statistics.mean(e2e_ms)}
+
+    peak, peak_kind = measured_peaks()
+    achieved = LOOP_BYTES_PER_NODE * n_nodes / (loop_ms / 1e3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = MEASURED_TRAFFIC.get(args.workload)
+    traffic = traffic["bytes"] if traffic and traffic.get("hash") == src_hash else None
+    roofline = {"bound": "hbm", "kernel": "k_persistent (Steps 2-3)", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_node": LOOP_BYTES_PER_NODE,
+                "loop_ms": loop_ms, "loop_share_of_step": loop_ms / ms_step,
+                "step_achieved_gbs": STEP_BYTES_PER_NODE * n_nodes / (ms_step / 1e3) / 1e9}
+    s0 = stats[-1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "nodes_per_gpu": n_nodes, "instances": len(insts),
+                       "tile": args.tile, "schedule": args.schedule, "order": args.order,
+                       "l2": "flushed between steps (256 MiB write outside the per-step events)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 5 * args.steps,
+            "solver_stats": {k: s0[k] for k in ("iters_update", "iters_remedy", "tiles_update",
+                                                "tiles_flagged", "tiles_remedy", "sweeps", "tiles_deferred")},
+            "wall_s_timed_region": wall, "kernel_source_hash": src_hash}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import numpy as np
+        import oracle
+        inst_c, desc = cpu_sample(args.workload)
+        Fc = inst_c.F.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.fmm(Fc, inst_c.h, inst_c.src_idx, inst_c.src_val)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": inst_c.n_nodes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="oscillating_256",
+                    choices=["oscillating_256", "point_source_128", "maze_512", "lognormal_batch64"])
+    ap.add_argument("--tile", default="auto")
+    ap.add_argument("--schedule", default="auto")
+    ap.add_argument("--order", type=float, default=0.0,
+                    help="list order: 0 default bucketed, >0 bucket width, <0 unordered")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * eikonal.h -- C ABI of libeikonal.so, a B300 (sm_103a) solver for the
+ * Eikonal equation ||grad phi|| = 1/F (eq. 3) on uniform 2D/3D grids by the
+ * improved fast iterative method (Algorithm 2, Sec. 3): a tile active-list
+ * value update without neighbour convergence checks (Step 2), then a remedy
+ * pass that finds and recomputes wrongly settled values (Step 3).
+ *
+ * Discretisation: first-order Godunov upwind scheme, eq. (4) in 2D and eq. (6)
+ * in 3D, isotropic spacing h (Alg 1.1 / Alg 1.3); every node's value is the
+ * exact root of its eq.-(6) residual given its neighbours.
+ *
+ * Layout (every entry point): a grid is row-major (nz, ny, nx), x fastest,
+ * flat index = (k*ny + j)*nx + i; a 2D grid has nz = 1.  Arrays of the
+ * solver's precision are float32 (EIK_FP32, default) or float64 (EIK_FP64,
+ * validation mode), both for F, source values, phi and adjoint arrays.
+ *
+ * Semantics:
+ *   - F > 0 is a speed; F == 0 is impassable (eq. 8 barrier): such a node keeps
+ *     phi = +inf unless it is a source.  Unreachable nodes get +inf.
+ *   - Sources are (flat index, value) pairs held fixed (Dirichlet, Alg 2
+ *     Step 1).  A duplicated index keeps the smaller value.
+ *
+ * Ownership: the caller owns every buffer.  Device pointers (F, phi, source
+ * arrays, workspace, adjoint arrays) must be device-accessible memory of the
+ * current device; "host" arrays are read during the call only.  The library
+ * allocates no device memory: it uses the caller's workspace, of at least
+ * eik_*workspace_size() bytes, 256-byte aligned.  All device work is enqueued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *
+ * Synchronisation and errors: argument errors are found on the host and
+ * returned before anything is enqueued.  Errors found on the device (a
+ * source index out of range, the iteration cap, an internal wait that timed
+ * out) are written into the workspace; they are returned, and the stream is
+ * synchronised, only when `stats` is non-NULL.  With stats == NULL the call
+ * returns after enqueuing (EIK_OK) and the result is ready when the stream
+ * reaches that point.  Calls that share a workspace must not overlap on the
+ * device.  eik_last_error() gives a thread-local message for the last
+ * non-zero return.
+ */
+#ifndef EIKONAL_H_
+#define EIKONAL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define EIK_OK 0
+#define EIK_ERR_ARG 1          /* invalid argument (dims, h, pointer, workspace, source index) */
+#define EIK_ERR_NOCONVERGE 2   /* iteration cap reached; phi holds valid upper bounds */
+#define EIK_ERR_CUDA 3         /* a CUDA launch or runtime call failed */
+#define EIK_ERR_DEVICE 4       /* a bounded device-side wait timed out; phi holds upper bounds */
+
+/* tile shapes (nodes per tile along x, y, z) */
+#define EIK_TILE_AUTO 0
+#define EIK_TILE_8x8x8 1
+#define EIK_TILE_4x4x4 2
+#define EIK_TILE_8x8x4 3
+#define EIK_TILE_16x16x1 4     /* 2D grids (nz == 1) only */
+#define EIK_TILE_8x4x4 5
+#define EIK_TILE_8x8x1 6       /* 2D grids (nz == 1) only */
+
+/* schedules of the iteration loops */
+#define EIK_SCHED_AUTO 0
+#define EIK_SCHED_PERSISTENT 1 /* one cooperative launch, bounded grid barriers */
+#define EIK_SCHED_HOSTLOOP 2   /* one launch per iteration, host reads the list size (synchronising) */
+
+/* precision */
+#define EIK_FP32 0
+#define EIK_FP64 1
+
+/* one grid: nx, ny, nz >= 1 nodes; isotropic spacing h > 0 */
+typedef struct {
+    int64_t nx, ny, nz;
+    double h;
+} eik_grid;
+
+/* per-call options; a zero-filled struct (or NULL) selects the defaults */
+typedef struct {
+    int32_t tile;         /* EIK_TILE_* (0 = auto: 8x8x1 for 2D, else 4x4x4) */
+    int32_t schedule;     /* EIK_SCHED_* (0 = auto: persistent when co-residency allows) */
+    int64_t max_iters;    /* cap per loop (update, remedy); 0 = automatic */
+    int32_t precision;    /* EIK_FP32 / EIK_FP64 */
+    int32_t skip_remedy;  /* 1 = stop after Step 2 (ablation; the result may be wrong) */
+    float order;          /* list order: 0 = default (bucketed, width 4), > 0 = bucket width in
+                             tile-crossing times, < 0 = unordered (every listed tile visited in
+                             every iteration, the schedule of Algorithm 2 as printed) */
+    int32_t reserved[3];  /* must be 0 */
+} eik_options;
+
+/* run statistics (filled when a stats pointer is passed; the call then synchronises) */
+typedef struct {
+    int64_t iters_update;     /* Step-2 iterations (tile-list passes) */
+    int64_t iters_remedy;     /* Step-3 loop iterations */
+    int64_t tiles_update;     /* tile visits in Step 2 */
+    int64_t tiles_flagged;    /* tiles put into Remedy by the Step-3 recomputation */
+    int64_t tiles_remedy;     /* tile visits in the Step-3 loop */
+    int64_t sweeps;           /* in-tile relaxation sweeps, summed over visits */
+    int64_t tiles_deferred;   /* listed tiles passed over by the ordered schedule */
+    int32_t status;           /* EIK_* code of the device-side run */
+    int32_t device_flags;     /* bit 0 cap hit, bit 1 wait timeout, bit 2 bad source, bit 3 list overflow */
+    double ms_total;          /* device time of the call, first to last kernel (CUDA events on `stream`) */
+    double ms_loop;           /* device time of the Step-2/3 loop launch(es) */
+} eik_stats;
+
+/*
+ * Workspace bytes for one grid / for a batch of B grids (host arrays), for the
+ * given options (tile shape and precision matter).  Returns 0 on invalid input.
+ */
+size_t eik_workspace_size(const eik_grid *grid, const eik_options *opt);
+size_t eik_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt);
+
+/*
+ * Solve eq. (6) on one grid by Algorithm 2 (Steps 1-3, Sec. 3.1.2).
+ *   grid     host; dims and spacing
+ *   F        device [nz][ny][nx]; speeds, F >= 0 (F == 0 impassable)
+ *   src_idx  device [n_src] int64 flat indices (checked on the device; an
+ *            index out of range is ignored and reported as EIK_ERR_ARG)
+ *   src_val  device [n_src] fixed values (precision type)
+ *   phi      device [nz][ny][nx] output, written completely
+ * Returns EIK_OK or an EIK_ERR_* code (see the synchronisation note above).
+ */
+int eik_solve(const eik_grid *grid, const void *F, const int64_t *src_idx, const void *src_val,
+              int64_t n_src, void *phi, void *workspace, size_t workspace_bytes, void *stream,
+              const eik_options *opt, eik_stats *stats);
+
+/*
+ * Solve B independent grids in one set of launches (one persistent launch for
+ * all of them).  Not in the paper: a batched form of the same method.
+ *   grids        host [B]
+ *   F_packed     device; instance b reads F_packed + F_offsets[b] (elements),
+ *                a [nz][ny][nx] block; instances may share a block
+ *   F_offsets    host [B] element offsets
+ *   src_idx/val  device; the sources of instance b are entries
+ *                src_offsets[b] .. src_offsets[b+1]-1 (flat indices into b's grid)
+ *   src_offsets  host [B+1], non-decreasing, src_offsets[0] = 0
+ *   phi_packed   device; instance b writes phi_packed + phi_offsets[b]
+ *   phi_offsets  host [B] element offsets (output blocks must not overlap)
+ * stats (nullable) receives totals over the batch.
+ */
+int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,
+                      const int64_t *src_idx, const void *src_val, const int64_t *src_offsets,
+                      void *phi_packed, const int64_t *phi_offsets, void *workspace,
+                      size_t workspace_bytes, void *stream, const eik_options *opt, eik_stats *stats);
+
+/* thread-local message describing the last non-zero return (never NULL) */
+const char *eik_last_error(void);
+
+/* library version string */
+const char *eik_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIKONAL_H_ */

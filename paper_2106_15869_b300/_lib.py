@@ -1,0 +1,136 @@
+"""ctypes binding of libeikonal.so: the C structs of include/eikonal.h and the
+entry points with the same names.  Argument marshalling only -- every step
+of the solve runs in the CUDA library.  Loading fails loudly when the
+library is missing or does not load; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeikonal.so")
+
+EIK_OK = 0
+EIK_ERR_ARG = 1
+EIK_ERR_NOCONVERGE = 2
+EIK_ERR_CUDA = 3
+EIK_ERR_DEVICE = 4
+
+TILES = {"auto": 0, "8x8x8": 1, "4x4x4": 2, "8x8x4": 3, "16x16x1": 4, "8x4x4": 5, "8x8x1": 6}
+SCHEDULES = {"auto": 0, "persistent": 1, "hostloop": 2}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+
+
+class eik_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("h", ctypes.c_double)]
+
+
+class eik_options(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("max_iters", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("skip_remedy", ctypes.c_int32), ("order", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class eik_stats(ctypes.Structure):
+    _fields_ = [("iters_update", ctypes.c_int64), ("iters_remedy", ctypes.c_int64),
+                ("tiles_update", ctypes.c_int64), ("tiles_flagged", ctypes.c_int64),
+                ("tiles_remedy", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("tiles_deferred", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("device_flags", ctypes.c_int32),
+                ("ms_total", ctypes.c_double), ("ms_loop", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EikonalError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"eikonal error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i64 = ctypes.c_int64
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def load():
+    """Load libeikonal.so (built in-tree by paper_2106_15869_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libeikonal.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_2106_15869_b300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    G = ctypes.POINTER(eik_grid)
+    O = ctypes.POINTER(eik_options)
+    S = ctypes.POINTER(eik_stats)
+    lib.eik_workspace_size.restype = _sz
+    lib.eik_workspace_size.argtypes = [G, O]
+    lib.eik_workspace_size_batched.restype = _sz
+    lib.eik_workspace_size_batched.argtypes = [_i64, G, O]
+    lib.eik_solve.restype = ctypes.c_int
+    lib.eik_solve.argtypes = [G, _vp, _vp, _vp, _i64, _vp, _vp, _sz, _vp, O, S]
+    lib.eik_solve_batched.restype = ctypes.c_int
+    lib.eik_solve_batched.argtypes = [_i64, G, _vp, _pi64, _vp, _vp, _pi64, _vp, _pi64, _vp, _sz,
+                                      _vp, O, S]
+    lib.eik_last_error.restype = ctypes.c_char_p
+    lib.eik_last_error.argtypes = []
+    lib.eik_version.restype = ctypes.c_char_p
+    lib.eik_version.argtypes = []
+    _optional_symbols(lib)
+    _lib = lib
+    return lib
+
+
+def _optional_symbols(lib):
+    """Declare signatures of entry points added after the forward solve."""
+    G = ctypes.POINTER(eik_grid)
+    O = ctypes.POINTER(eik_options)
+    S = ctypes.POINTER(eik_stats)
+    if hasattr(lib, "eik_adjoint_workspace_size_batched"):
+        lib.eik_adjoint_workspace_size_batched.restype = _sz
+        lib.eik_adjoint_workspace_size_batched.argtypes = [_i64, G, O]
+    if hasattr(lib, "eik_adjoint_batched"):
+        lib.eik_adjoint_batched.restype = ctypes.c_int
+        lib.eik_adjoint_batched.argtypes = [_i64, G, _vp, _pi64, _vp, _pi64, _vp, _vp, _pi64, _vp,
+                                            _pi64, _vp, _sz, _vp, O, S]
+
+
+def check(rc: int):
+    if rc != EIK_OK:
+        msg = load().eik_last_error().decode(errors="replace")
+        raise EikonalError(rc, msg)
+
+
+def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=False,
+                 max_iters=0, order=0.0) -> eik_options:
+    o = eik_options()
+    o.tile = TILES[tile] if isinstance(tile, str) else int(tile)
+    o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.skip_remedy = int(bool(skip_remedy))
+    o.max_iters = int(max_iters)
+    o.order = float(order)
+    return o
+
+
+def grids_array(dims_h):
+    """[(nx, ny, nz, h), ...] -> ctypes array of eik_grid."""
+    arr = (eik_grid * len(dims_h))()
+    for q, (nx, ny, nz, h) in enumerate(dims_h):
+        arr[q].nx, arr[q].ny, arr[q].nz, arr[q].h = int(nx), int(ny), int(nz), float(h)
+    return arr
+
+
+def i64_array(vals):
+    arr = (ctypes.c_int64 * len(vals))()
+    for q, v in enumerate(vals):
+        arr[q] = int(v)
+    return arr

@@ -1,0 +1,180 @@
+"""Python API over the C ABI: torch tensors in, torch tensors out.
+
+torch supplies device memory (the caching allocator) and the current CUDA
+stream; every step of the solve runs in libeikonal.so.  A CPU tensor given to
+``solve`` is copied to the current CUDA device and the result copied back
+(the end-to-end path); there is no CPU solver.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_DT = {torch.float32: "fp32", torch.float64: "fp64"}
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dims(F: torch.Tensor):
+    if F.dim() == 2:
+        return int(F.shape[1]), int(F.shape[0]), 1
+    if F.dim() == 3:
+        return int(F.shape[2]), int(F.shape[1]), int(F.shape[0])
+    raise ValueError("F must be (ny, nx) or (nz, ny, nx)")
+
+
+def _as_index(src_idx, device) -> torch.Tensor:
+    t = torch.as_tensor(np.asarray(src_idx, dtype=np.int64).reshape(-1)) if not torch.is_tensor(src_idx) \
+        else src_idx.reshape(-1).to(torch.int64)
+    return t.to(device, non_blocking=True).contiguous()
+
+
+def _as_values(src_val, n, dtype, device) -> torch.Tensor:
+    if src_val is None:
+        return torch.zeros(n, dtype=dtype, device=device)
+    t = src_val if torch.is_tensor(src_val) else torch.as_tensor(np.asarray(src_val, dtype=np.float64))
+    t = t.reshape(-1).to(device=device, dtype=dtype)
+    if t.numel() != n:
+        raise ValueError("src_val must have one value per source index")
+    return t.contiguous()
+
+
+class Workspace:
+    """A reusable, growable device workspace (one per stream is the usual pattern)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+_default_ws: dict = {}
+
+
+def _workspace(device, nbytes, ws: Workspace | None):
+    if ws is None:
+        key = (device.index, torch.cuda.current_stream(device).cuda_stream)
+        ws = _default_ws.get(key)
+        if ws is None:
+            ws = _default_ws[key] = Workspace(device)
+    buf = ws.get(nbytes)
+    if buf.data_ptr() % 256:
+        raise RuntimeError("workspace is not 256-byte aligned")
+    return buf
+
+
+def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", schedule="auto",
+          skip_remedy=False, max_iters=0, order=0.0, return_stats=False, workspace: Workspace | None = None,
+          out: torch.Tensor | None = None):
+    """Arrival times phi of ||grad phi|| = 1/F with fixed values at the sources.
+
+    F: (ny, nx) or (nz, ny, nx) float32 (or float64 = FP64 validation mode)
+    speeds, F == 0 impassable; src_idx: flat indices; src_val: values
+    (default 0); h: grid spacing.  Returns phi with F's shape, dtype and device
+    (+inf where unreachable); with return_stats also a dict of run statistics
+    (this synchronises the stream).  order: 0 = default bucketed list order,
+    > 0 = bucket width in tile-crossing times, < 0 = unordered lists (every
+    listed tile visited in every iteration, as Algorithm 2 is printed).
+    """
+    if F.dtype not in _DT:
+        raise TypeError("F must be float32 or float64")
+    host = not F.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else F.device
+    Fd = F.to(dev, non_blocking=True).contiguous() if host else F.contiguous()
+    nx, ny, nz = _dims(Fd)
+    idx = _as_index(src_idx, dev)
+    val = _as_values(src_val, idx.numel(), Fd.dtype, dev)
+    lib = _lib.load()
+    g = _lib.grids_array([(nx, ny, nz, h)])
+    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order)
+    nbytes = lib.eik_workspace_size(g, ctypes.byref(opt))
+    if nbytes == 0:
+        raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grid or options")
+    with torch.cuda.device(dev):
+        buf = _workspace(dev, nbytes, workspace)
+        phi = out if out is not None else torch.empty_like(Fd)
+        st = _lib.eik_stats()
+        rc = lib.eik_solve(g, Fd.data_ptr(), idx.data_ptr() if idx.numel() else None,
+                           val.data_ptr() if idx.numel() else None, idx.numel(), phi.data_ptr(),
+                           buf.data_ptr(), buf.numel(), _stream_ptr(), ctypes.byref(opt),
+                           ctypes.byref(st) if return_stats else None)
+        _lib.check(rc)
+    if host:
+        phi = phi.to("cpu")
+    return (phi, st.as_dict()) if return_stats else phi
+
+
+def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, max_iters=0, order=0.0,
+                  return_stats=False, workspace: Workspace | None = None, shared_F: bool = False):
+    """Solve many independent grids in one set of launches.
+
+    problems: list of (F, src_idx, h) or (F, src_idx, h, src_val); all F on the
+    same CUDA device with the same dtype.  With shared_F=True every problem
+    uses the first problem's F (one copy, read by all instances; e.g. many
+    sources on one speed map).  Returns a list of phi tensors.
+    """
+    if not problems:
+        return ([], {}) if return_stats else []
+    F0 = problems[0][0]
+    dev, dtype = F0.device, F0.dtype
+    if dtype not in _DT or not F0.is_cuda:
+        raise TypeError("F must be a float32/float64 CUDA tensor")
+    dims, Fs, idxs, vals = [], [], [], []
+    for p in problems:
+        F, si, h = p[0], p[1], p[2]
+        sv = p[3] if len(p) > 3 else None
+        if shared_F:
+            F = F0
+        if F.device != dev or F.dtype != dtype:
+            raise ValueError("all F must share device and dtype")
+        nx, ny, nz = _dims(F)
+        dims.append((nx, ny, nz, h))
+        Fs.append(F)
+        i = _as_index(si, dev)
+        idxs.append(i)
+        vals.append(_as_values(sv, i.numel(), dtype, dev))
+    sizes = [d[0] * d[1] * d[2] for d in dims]
+    phi_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    if shared_F:
+        F_packed = F0.contiguous().reshape(-1)
+        F_off = np.zeros(len(problems), dtype=np.int64)
+    else:
+        F_packed = torch.cat([F.contiguous().reshape(-1) for F in Fs])
+        F_off = phi_off
+    nsrc = [i.numel() for i in idxs]
+    src_off = np.concatenate([[0], np.cumsum(nsrc)]).astype(np.int64)
+    src_idx = torch.cat(idxs) if sum(nsrc) else torch.zeros(0, dtype=torch.int64, device=dev)
+    src_val = torch.cat(vals) if sum(nsrc) else torch.zeros(0, dtype=dtype, device=dev)
+    lib = _lib.load()
+    g = _lib.grids_array(dims)
+    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order)
+    B = len(problems)
+    nbytes = lib.eik_workspace_size_batched(B, g, ctypes.byref(opt))
+    if nbytes == 0:
+        raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grids or options")
+    with torch.cuda.device(dev):
+        buf = _workspace(dev, nbytes, workspace)
+        phi_packed = torch.empty(int(sum(sizes)), dtype=dtype, device=dev)
+        st = _lib.eik_stats()
+        rc = lib.eik_solve_batched(B, g, F_packed.data_ptr(), _lib.i64_array(F_off),
+                                   src_idx.data_ptr() if src_idx.numel() else None,
+                                   src_val.data_ptr() if src_idx.numel() else None,
+                                   _lib.i64_array(src_off), phi_packed.data_ptr(), _lib.i64_array(phi_off),
+                                   buf.data_ptr(), buf.numel(), _stream_ptr(), ctypes.byref(opt),
+                                   ctypes.byref(st) if return_stats else None)
+        _lib.check(rc)
+    outs = []
+    for q, F in enumerate(Fs):
+        outs.append(phi_packed[phi_off[q]:phi_off[q] + sizes[q]].view(F.shape))
+    return (outs, st.as_dict()) if return_stats else outs

@@ -1,0 +1,449 @@
+// eik_api.cu -- the C ABI of libeikonal.so (declared in include/eikonal.h):
+// argument checks, workspace layout, template dispatch over precision and
+// tile shape, and the two loop schedules (persistent cooperative launch, or
+// one launch per iteration with a host-read list size).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/eikonal.h"
+#include "eik_common.cuh"
+#include "eik_forward.cuh"
+
+using namespace eik;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(EIK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define EIK_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct TileShape {
+    int bx, by, bz;
+};
+
+TileShape tile_shape(int tile) {
+    switch (tile) {
+        case EIK_TILE_4x4x4: return {4, 4, 4};
+        case EIK_TILE_8x8x4: return {8, 8, 4};
+        case EIK_TILE_16x16x1: return {16, 16, 1};
+        case EIK_TILE_8x4x4: return {8, 4, 4};
+        case EIK_TILE_8x8x1: return {8, 8, 1};
+        default: return {8, 8, 8};
+    }
+}
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Opts {
+    int tile, schedule, precision, skip_remedy;
+    long long max_iters;
+    float order;           // <= 0: unordered lists (every listed tile visited each iteration)
+};
+
+constexpr float kDefaultOrder = 4.0f;   // bucket width (tile-crossing times) of the default schedule
+
+bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out) {
+    out.tile = o ? o->tile : EIK_TILE_AUTO;
+    out.schedule = o ? o->schedule : EIK_SCHED_AUTO;
+    out.precision = o ? o->precision : EIK_FP32;
+    out.skip_remedy = o ? o->skip_remedy : 0;
+    out.max_iters = o ? o->max_iters : 0;
+    const float ord = o ? o->order : 0.0f;
+    if (!(ord == ord)) return false;                       // NaN
+    out.order = ord == 0.0f ? kDefaultOrder : (ord < 0.0f ? 0.0f : ord);
+    if (o) {
+        for (int q = 0; q < 3; ++q)
+            if (o->reserved[q] != 0) return false;
+    }
+    if (out.precision != EIK_FP32 && out.precision != EIK_FP64) return false;
+    if (out.schedule < 0 || out.schedule > EIK_SCHED_HOSTLOOP) return false;
+    if (out.tile < 0 || out.tile > EIK_TILE_8x8x1) return false;
+    bool all2d = true;
+    for (int64_t b = 0; b < B; ++b) all2d = all2d && grids[b].nz == 1;
+    if (out.tile == EIK_TILE_AUTO) out.tile = all2d ? EIK_TILE_8x8x1 : EIK_TILE_4x4x4;
+    if ((out.tile == EIK_TILE_16x16x1 || out.tile == EIK_TILE_8x8x1) && !all2d) return false;
+    if (out.max_iters < 0) return false;
+    return true;
+}
+
+// workspace regions (byte offsets), all 256-byte aligned
+struct Layout {
+    size_t ctl, desc, inst_acc, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t, total;
+    long long n_tiles;
+    std::vector<InstDesc> desc_host;
+};
+
+bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std::string *why) {
+    const TileShape ts = tile_shape(o.tile);
+    const size_t esz = o.precision == EIK_FP64 ? 8 : 4;
+    const long long V = (long long)ts.bx * ts.by * ts.bz;
+    L.desc_host.resize((size_t)B);
+    long long tiles = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        const eik_grid &g = grids[b];
+        if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > (1ll << 30) || g.ny > (1ll << 30) || g.nz > (1ll << 30)) {
+            if (why) *why = "grid " + std::to_string(b) + ": dims must be in [1, 2^30]";
+            return false;
+        }
+        if (!(g.h > 0.0) || !(g.h < 1e300)) {
+            if (why) *why = "grid " + std::to_string(b) + ": h must be finite and > 0";
+            return false;
+        }
+        InstDesc &d = L.desc_host[(size_t)b];
+        std::memset(&d, 0, sizeof(d));
+        d.nx = (int)g.nx; d.ny = (int)g.ny; d.nz = (int)g.nz;
+        d.tx = (int)((g.nx + ts.bx - 1) / ts.bx);
+        d.ty = (int)((g.ny + ts.by - 1) / ts.by);
+        d.tz = (int)((g.nz + ts.bz - 1) / ts.bz);
+        d.tile_base = tiles;
+        d.h = g.h;
+        tiles += (long long)d.tx * d.ty * d.tz;
+        if (tiles >= (1ll << 31) - 1) {
+            if (why) *why = "too many tiles (more than 2^31 - 2)";
+            return false;
+        }
+    }
+    L.n_tiles = tiles;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
+    L.ctl = take(sizeof(Ctl));
+    L.desc = take(sizeof(InstDesc) * (size_t)B);
+    L.inst_acc = take(2 * sizeof(double) * (size_t)B);
+    L.inst_scale = take(sizeof(float) * (size_t)B);
+    L.tile_inst = take(4 * (size_t)tiles);
+    L.tile_nb = take(4 * 6 * (size_t)tiles);
+    L.tstate = take(4 * (size_t)tiles);
+    L.tstamp = take(4 * (size_t)tiles);
+    L.tkey = take(2 * 4 * (size_t)tiles);
+    L.list0 = take(4 * (size_t)tiles);
+    L.list1 = take(4 * (size_t)tiles);
+    L.phi_t = take(esz * (size_t)(tiles * V));
+    L.tau_t = take(esz * (size_t)(tiles * V));
+    L.total = off;
+    return true;
+}
+
+long long auto_max_iters(const Layout &L) {
+    long long m = 0;
+    for (const InstDesc &d : L.desc_host) {
+        const long long s = (long long)d.tx + d.ty + d.tz;
+        if (s > m) m = s;
+    }
+    return 64 * m + 4096;
+}
+
+struct DevInfo {
+    int dev = -1, sms = 0, coop = 0;
+};
+
+int device_info(DevInfo &di) {
+    EIK_CUDA(cudaGetDevice(&di.dev), "cudaGetDevice");
+    EIK_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, di.dev), "cudaDeviceGetAttribute");
+    EIK_CUDA(cudaDeviceGetAttribute(&di.coop, cudaDevAttrCooperativeLaunch, di.dev), "cudaDeviceGetAttribute");
+    return EIK_OK;
+}
+
+int upload_desc(InstDesc *ddesc, double *inst_acc, const std::vector<InstDesc> &h, cudaStream_t st) {
+    const int B = (int)h.size();
+    for (int first = 0; first < B; first += kMaxInstPerLaunch) {
+        DescChunk c;
+        std::memset(&c, 0, sizeof(c));
+        c.first = first;
+        c.count = std::min(kMaxInstPerLaunch, B - first);
+        for (int q = 0; q < c.count; ++q) c.d[q] = h[(size_t)(first + q)];
+        k_write_desc<<<1, kMaxInstPerLaunch, 0, st>>>(ddesc, inst_acc, c);
+        EIK_CUDA(cudaGetLastError(), "k_write_desc launch");
+    }
+    return EIK_OK;
+}
+
+// CUDA events bracketing the phases of one call (created only when stats are requested)
+struct PhaseEvents {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool on = false;
+    int create() {
+        for (auto &x : e) EIK_CUDA(cudaEventCreate(&x), "cudaEventCreate");
+        on = true;
+        return EIK_OK;
+    }
+    void record(int q, cudaStream_t st) {
+        if (on) (void)cudaEventRecord(e[q], st);
+    }
+    ~PhaseEvents() {
+        for (auto &x : e)
+            if (x) (void)cudaEventDestroy(x);
+    }
+};
+
+int finish_stats(Ctl *dctl, cudaStream_t st, eik_stats *stats, PhaseEvents *pe) {
+    Ctl h;
+    EIK_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "stats copy");
+    EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+    if (pe && pe->on) {
+        float a = 0.f, b = 0.f;
+        EIK_CUDA(cudaEventElapsedTime(&a, pe->e[0], pe->e[3]), "cudaEventElapsedTime");
+        EIK_CUDA(cudaEventElapsedTime(&b, pe->e[1], pe->e[2]), "cudaEventElapsedTime");
+        stats->ms_total = a;
+        stats->ms_loop = b;
+    }
+    stats->iters_update = h.iters_update;
+    stats->iters_remedy = h.iters_remedy;
+    stats->tiles_update = h.tiles_update;
+    stats->tiles_flagged = h.tiles_flagged;
+    stats->tiles_remedy = h.tiles_remedy;
+    stats->sweeps = h.sweeps;
+    stats->tiles_deferred = h.tiles_deferred;
+    stats->device_flags = h.flags;
+    int code = EIK_OK;
+    if (h.flags & kFlagTimeout) code = fail(EIK_ERR_DEVICE, "a device-side wait timed out");
+    else if (h.flags & kFlagOverflow) code = fail(EIK_ERR_DEVICE, "internal list overflow");
+    else if (h.flags & kFlagBadSource) code = fail(EIK_ERR_ARG, "a source index lies outside its grid");
+    else if (h.flags & kFlagCap) code = fail(EIK_ERR_NOCONVERGE, "iteration cap reached");
+    stats->status = code;
+    return code;
+}
+
+template <class T, int BX, int BY, int BZ>
+int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const int64_t *src_idx,
+                const void *src_val, int64_t n_src, void *phi, cudaStream_t st, eik_stats *stats) {
+    FwdParams<T> P;
+    P.desc = reinterpret_cast<const InstDesc *>(ws + L.desc);
+    P.B = (int)L.desc_host.size();
+    P.n_tiles = (int)L.n_tiles;
+    P.tile_inst = reinterpret_cast<int *>(ws + L.tile_inst);
+    P.tile_nb = reinterpret_cast<int *>(ws + L.tile_nb);
+    P.tstate = reinterpret_cast<int *>(ws + L.tstate);
+    P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
+    P.tkey = reinterpret_cast<unsigned *>(ws + L.tkey);
+    P.inst_scale = reinterpret_cast<float *>(ws + L.inst_scale);
+    P.inst_acc = reinterpret_cast<double *>(ws + L.inst_acc);
+    P.ordered = o.order > 0.0f ? 1 : 0;
+    P.order = o.order;
+    P.list0 = reinterpret_cast<int *>(ws + L.list0);
+    P.list1 = reinterpret_cast<int *>(ws + L.list1);
+    P.phi_t = reinterpret_cast<T *>(ws + L.phi_t);
+    P.tau_t = reinterpret_cast<T *>(ws + L.tau_t);
+    P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    P.max_iters = o.max_iters > 0 ? o.max_iters : auto_max_iters(L);
+    P.skip_remedy = o.skip_remedy;
+    P.max_sweeps = 4 * (BX + BY + BZ) + 8;
+    P.F = static_cast<const T *>(F);
+    P.src_idx = reinterpret_cast<const long long *>(src_idx);
+    P.src_val = static_cast<const T *>(src_val);
+    P.n_src = n_src;
+    P.phi_out = static_cast<T *>(phi);
+    constexpr int V = BX * BY * BZ;
+    static_assert(sizeof(Ctl) / sizeof(int) <= V, "control block zeroing needs V >= ints in Ctl");
+
+    PhaseEvents pe;
+    int rc = EIK_OK;
+    if (stats && (rc = pe.create())) return rc;
+    pe.record(0, st);
+    rc = upload_desc(const_cast<InstDesc *>(P.desc), P.inst_acc, L.desc_host, st);
+    if (rc) return rc;
+    k_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_init launch");
+    if (P.ordered) {
+        k_scale<BX, BY, BZ><<<(P.B + 127) / 128, 128, 0, st>>>(P.desc, P.inst_acc, P.inst_scale, P.B, P.order);
+        EIK_CUDA(cudaGetLastError(), "k_scale launch");
+    }
+    if (n_src > 0) {
+        k_sources<T, BX, BY, BZ><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(P);
+        EIK_CUDA(cudaGetLastError(), "k_sources launch");
+    }
+
+    DevInfo di;
+    rc = device_info(di);
+    if (rc) return rc;
+    constexpr int CTA = 32 * kWarpsPerCta;
+    int per_sm = 0;
+    EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<T, BX, BY, BZ>, CTA, 0),
+             "occupancy query");
+    int sched = o.schedule;
+    if (sched == EIK_SCHED_AUTO) sched = (di.coop && per_sm > 0) ? EIK_SCHED_PERSISTENT : EIK_SCHED_HOSTLOOP;
+
+    bool done = false;
+    pe.record(1, st);
+    if (sched == EIK_SCHED_PERSISTENT) {
+        int grid = per_sm * di.sms;
+        const int need = (int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        void *args[] = {&P};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_persistent<T, BX, BY, BZ>, dim3(grid),
+                                                    dim3(CTA), args, 0, st);
+        if (e == cudaSuccess) {
+            done = true;
+        } else if (o.schedule == EIK_SCHED_PERSISTENT) {
+            return cuda_fail(e, "cooperative launch");
+        } else {
+            (void)cudaGetLastError();   // clear, then fall back to the host loop
+        }
+    }
+    if (!done) {
+        // host loop: one launch per iteration, the list size is read back each time
+        const int grid_cap = std::max(1, per_sm * di.sms);
+        Ctl *dctl = P.ctl;
+        int n = 0;
+        EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+        EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+        long long it = 0, r = 0;
+        bool capped = false;
+        while (n > 0) {
+            if (it >= P.max_iters) { capped = true; break; }
+            k_update_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(P, (int)it);
+            EIK_CUDA(cudaGetLastError(), "k_update_iter launch");
+            ++it;
+            EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[it % 3], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+            EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+        }
+        if (!capped && !P.skip_remedy) {
+            k_detect<T, BX, BY, BZ><<<std::min((int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta), grid_cap), CTA, 0, st>>>(P);
+            EIK_CUDA(cudaGetLastError(), "k_detect launch");
+            EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+            EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+            while (n > 0) {
+                if (r >= P.max_iters) { capped = true; break; }
+                k_remedy_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(P, (int)r);
+                EIK_CUDA(cudaGetLastError(), "k_remedy_iter launch");
+                ++r;
+                EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[r % 3], sizeof(int), cudaMemcpyDeviceToHost, st),
+                         "count copy");
+                EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+            }
+        }
+        long long iters[2] = {it, r};
+        EIK_CUDA(cudaMemcpyAsync(&dctl->iters_update, iters, sizeof(iters), cudaMemcpyHostToDevice, st),
+                 "iters copy");
+        if (capped) {
+            int f = kFlagCap;
+            int cur = 0;
+            EIK_CUDA(cudaMemcpyAsync(&cur, &dctl->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flags copy");
+            EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+            f |= cur;
+            EIK_CUDA(cudaMemcpyAsync(&dctl->flags, &f, sizeof(int), cudaMemcpyHostToDevice, st), "flags copy");
+        }
+        EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+    }
+    pe.record(2, st);
+    k_unpack<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_unpack launch");
+    pe.record(3, st);
+    if (stats) return finish_stats(P.ctl, st, stats, &pe);
+    return EIK_OK;
+}
+
+template <class T>
+int dispatch_tile(const Layout &L, const Opts &o, char *ws, const void *F, const int64_t *si, const void *sv,
+                  int64_t ns, void *phi, cudaStream_t st, eik_stats *stats) {
+    switch (o.tile) {
+        case EIK_TILE_4x4x4: return run_forward<T, 4, 4, 4>(L, o, ws, F, si, sv, ns, phi, st, stats);
+        case EIK_TILE_8x8x4: return run_forward<T, 8, 8, 4>(L, o, ws, F, si, sv, ns, phi, st, stats);
+        case EIK_TILE_16x16x1: return run_forward<T, 16, 16, 1>(L, o, ws, F, si, sv, ns, phi, st, stats);
+        case EIK_TILE_8x4x4: return run_forward<T, 8, 4, 4>(L, o, ws, F, si, sv, ns, phi, st, stats);
+        case EIK_TILE_8x8x1: return run_forward<T, 8, 8, 1>(L, o, ws, F, si, sv, ns, phi, st, stats);
+        default: return run_forward<T, 8, 8, 8>(L, o, ws, F, si, sv, ns, phi, st, stats);
+    }
+}
+
+int solve_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F_offsets, const int64_t *src_idx,
+               const void *src_val, const int64_t *src_offsets, void *phi, const int64_t *phi_offsets, void *ws,
+               size_t ws_bytes, void *stream, const eik_options *opt, eik_stats *stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (B < 1) return fail(EIK_ERR_ARG, "batch size must be >= 1");
+    if (B > (1ll << 24)) return fail(EIK_ERR_ARG, "batch size too large");
+    if (!grids) return fail(EIK_ERR_ARG, "grids is NULL");
+    Opts o;
+    if (!read_opts(opt, B, grids, o)) return fail(EIK_ERR_ARG, "invalid options");
+    Layout L;
+    std::string why;
+    if (!make_layout(B, grids, o, L, &why)) return fail(EIK_ERR_ARG, "%s", why.c_str());
+    if (!ws) return fail(EIK_ERR_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(EIK_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(EIK_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+    if (!F || !phi) return fail(EIK_ERR_ARG, "F and phi must be non-NULL");
+    if (src_offsets[0] != 0) return fail(EIK_ERR_ARG, "src_offsets[0] must be 0");
+    for (int64_t b = 0; b < B; ++b) {
+        if (src_offsets[b + 1] < src_offsets[b]) return fail(EIK_ERR_ARG, "src_offsets must be non-decreasing");
+        if (F_offsets[b] < 0 || phi_offsets[b] < 0) return fail(EIK_ERR_ARG, "offsets must be >= 0");
+        InstDesc &d = L.desc_host[(size_t)b];
+        d.in_off = F_offsets[b];
+        d.out_off = phi_offsets[b];
+        d.src_begin = src_offsets[b];
+        d.src_end = src_offsets[b + 1];
+    }
+    const int64_t n_src = src_offsets[B];
+    if (n_src > 0 && (!src_idx || !src_val)) return fail(EIK_ERR_ARG, "source arrays must be non-NULL");
+    if (n_src >= (1ll << 40)) return fail(EIK_ERR_ARG, "too many sources");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(ws);
+    if (o.precision == EIK_FP64)
+        return dispatch_tile<double>(L, o, w, F, src_idx, src_val, n_src, phi, st, stats);
+    return dispatch_tile<float>(L, o, w, F, src_idx, src_val, n_src, phi, st, stats);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t eik_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt) {
+    if (B < 1 || !grids) return 0;
+    Opts o;
+    if (!read_opts(opt, B, grids, o)) return 0;
+    Layout L;
+    if (!make_layout(B, grids, o, L, nullptr)) return 0;
+    return L.total;
+}
+
+size_t eik_workspace_size(const eik_grid *grid, const eik_options *opt) {
+    return eik_workspace_size_batched(1, grid, opt);
+}
+
+int eik_solve(const eik_grid *grid, const void *F, const int64_t *src_idx, const void *src_val, int64_t n_src,
+              void *phi, void *workspace, size_t workspace_bytes, void *stream, const eik_options *opt,
+              eik_stats *stats) {
+    if (n_src < 0) return fail(EIK_ERR_ARG, "n_src must be >= 0");
+    const int64_t zero = 0;
+    const int64_t so[2] = {0, n_src};
+    return solve_impl(1, grid, F, &zero, src_idx, src_val, so, phi, &zero, workspace, workspace_bytes, stream, opt,
+                      stats);
+}
+
+int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,
+                      const int64_t *src_idx, const void *src_val, const int64_t *src_offsets, void *phi_packed,
+                      const int64_t *phi_offsets, void *workspace, size_t workspace_bytes, void *stream,
+                      const eik_options *opt, eik_stats *stats) {
+    if (!F_offsets || !src_offsets || !phi_offsets) return fail(EIK_ERR_ARG, "offset arrays must be non-NULL");
+    return solve_impl(B, grids, F_packed, F_offsets, src_idx, src_val, src_offsets, phi_packed, phi_offsets,
+                      workspace, workspace_bytes, stream, opt, stats);
+}
+
+const char *eik_last_error(void) { return g_err.c_str(); }
+
+const char *eik_version(void) { return "eikonal-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// eik_common.cuh -- shared device definitions of the iFIM CUDA path (sm_103a).
+//
+// Data layout in HBM (per solve, inside the caller's workspace):
+//   phi_t, tau_t   bricked: tile g occupies [g*V, (g+1)*V), V = BX*BY*BZ nodes,
+//                  x fastest inside the tile; tiles of an instance are ordered
+//                  (tz, ty, tx) and instances follow each other (tile_base).
+//                  Nodes of a boundary tile that lie outside the grid carry
+//                  tau = +inf and phi = +inf forever.
+//   tau            h / F per node (+inf where F == 0, eq. 8 barrier); a fixed
+//                  source node carries tau = -1 (a sign marker, never used in
+//                  arithmetic).
+//   tstate         per tile: 0 Distant, 1 Active, 2 Source (Algorithm 2 sets,
+//                  taken at tile granularity)
+//   tstamp         per tile: remedy-list membership stamp (iteration + 1)
+//   list0/list1    tile-id lists (Active or Remedy), ping-pong by iteration
+//   Ctl            counters, barrier word, flags and statistics
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eik {
+
+constexpr int kMaxInstPerLaunch = 128;       // descriptors passed by value per launch
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s bound on every device wait
+
+// device flag bits (eik_stats.device_flags)
+constexpr int kFlagCap = 1;          // iteration cap reached
+constexpr int kFlagTimeout = 2;      // a bounded wait gave up
+constexpr int kFlagBadSource = 4;    // a source index outside its grid (ignored)
+constexpr int kFlagOverflow = 8;     // a list push beyond capacity (internal error)
+
+enum TileState : int { kDistant = 0, kActive = 1, kSource = 2 };
+
+struct InstDesc {
+    int32_t nx, ny, nz, pad0;
+    int32_t tx, ty, tz, pad1;     // tiles per axis
+    int64_t tile_base;            // first global tile id of this instance
+    int64_t in_off;               // element offset of F (and of r in the adjoint)
+    int64_t out_off;              // element offset of phi (and of g in the adjoint)
+    int64_t src_begin, src_end;   // entries of the packed source arrays
+    double h;
+};
+
+struct DescChunk {                // by-value kernel parameter (capture-safe upload)
+    InstDesc d[kMaxInstPerLaunch];
+    int first, count;
+};
+
+struct Ctl {
+    unsigned long long bar;       // grid-barrier arrivals (monotone within a launch)
+    int abort;                    // a barrier wait timed out: every block leaves
+    int flags;                    // kFlag* bits
+    int cnt[3];                   // Step-2 list sizes, slot = iteration % 3
+    int rcnt[3];                  // Step-3 list sizes
+    unsigned kmin[3];             // Step-2 smallest key listed for iteration it (slot it % 3)
+    unsigned rkmin[3];            // Step-3 smallest key listed for iteration r
+    long long iters_update, iters_remedy;
+    long long tiles_update, tiles_flagged, tiles_remedy, sweeps, tiles_deferred;
+    long long pad1[2];
+};
+static_assert(sizeof(Ctl) <= 256, "the control block is zeroed by 64 threads");
+
+// Ordered-float encoding for atomicMin on keys: monotone as unsigned.
+__device__ __forceinline__ unsigned key_enc(float k) {
+    const unsigned b = __float_as_uint(k);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_dec(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+constexpr unsigned kKeyInf = 0xff800000u;   // key_enc(+inf)
+
+// ----------------------------------------------------------------- helpers
+template <class T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ unsigned ld_volatile_u(const unsigned *p) { return *(const volatile unsigned *)p; }
+
+// Exact root of eq. (6) given the per-axis upwind minima and tau = h/F:
+//   sum_d ((u - a_d)^+)^2 = tau^2, a1 <= a2 <= a3 sorted.
+// One-sided u = a1 + tau while u <= a2; two-sided while u <= a3; else
+// three-sided.  The roots are formed relative to a1 (d2 = a2 - a1,
+// d3 = a3 - a1) so that no large sums cancel in FP32:
+//   two-sided   u = a1 + (d2 + sqrt(2 tau^2 - d2^2)) / 2
+//   three-sided u = a1 + (d2 + d3 + sqrt(3 tau^2 - d2^2 - d3^2 - (d3 - d2)^2)) / 3
+// The thresholds are the validity conditions of the "^+" equation (Alg 1.1
+// and Alg 1.3 print others).  a1 = +inf or tau = +inf yields +inf.
+template <class T>
+__device__ __forceinline__ T local_solve(T ax, T ay, T az, T tau) {
+    const T lo = vmin(ax, ay), hi = vmax(ax, ay);
+    const T a1 = vmin(lo, az);
+    const T a3 = vmax(hi, az);
+    const T a2 = vmax(lo, vmin(hi, az));
+    T u = a1 + tau;
+    if (u <= a2) return u;
+    const T d2 = a2 - a1;
+    u = a1 + T(0.5) * (d2 + vsqrt(T(2) * tau * tau - d2 * d2));
+    if (u <= a3) return u;
+    const T d3 = a3 - a1, d32 = d3 - d2;
+    T disc = T(3) * tau * tau - (d2 * d2 + d3 * d3 + d32 * d32);
+    disc = vmax(disc, T(0));
+    return a1 + (d2 + d3 + vsqrt(disc)) * (T(1) / T(3));
+}
+
+// Device-wide barrier for a cooperative launch.  Every wait is bounded by
+// kWaitLimitNs; on a timeout the block raises ctl->abort and every block
+// leaves at its next barrier.  Returns false when the launch must stop.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned long long &target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        atomicAdd(&ctl->bar, 1ull);
+        const unsigned long long t0 = globaltimer();
+        int ok = 1;
+        while (ld_acquire(&ctl->bar) < target) {
+            if (ld_volatile(&ctl->abort)) { ok = 0; break; }
+            if (globaltimer() - t0 > kWaitLimitNs) {
+                atomicOr(&ctl->flags, kFlagTimeout);
+                atomicExch(&ctl->abort, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(40);
+        }
+        __threadfence();
+        if (ld_volatile(&ctl->abort)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// binary search: instance whose [tile_base, next tile_base) holds tile g
+__device__ __forceinline__ int find_inst_by_tile(const InstDesc *desc, int B, long long g) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// binary search: instance whose [src_begin, src_end) holds source entry s
+__device__ __forceinline__ int find_inst_by_src(const InstDesc *desc, int B, long long s) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].src_begin <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace eik

@@ -1,0 +1,241 @@
+"""GPU parity of the forward solve (C ABI via the thin Python binding) against
+the FP64 CPU oracle, element by element on the same seeded inputs.
+
+Tolerances: FP32 path max|phi_gpu - phi_oracle| <= 1e-4 * max(phi) over finite
+nodes, FP64 validation mode <= 1e-10 * max(phi); +inf (unreachable) must
+match exactly.  The oracle is fed the float32-rounded speeds so that only the
+solver's arithmetic differs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_15869_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL64 = 1e-10
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_solve(inst, dtype="fp32", **kw):
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    tdt = torch.float32 if dtype == "fp32" else torch.float64
+    F = torch.as_tensor(inst.F, dtype=tdt).cuda()
+    phi, st = api.solve(F, inst.src_idx, inst.h, inst.src_val, return_stats=True, **kw)
+    assert st["status"] == 0, st
+    return phi.cpu().double().numpy(), st
+
+
+def oracle_phi(inst, dtype="fp32"):
+    F = inst.F.astype(np.float32).astype(np.float64) if dtype == "fp32" else inst.F
+    val = inst.src_val.astype(np.float32).astype(np.float64) if dtype == "fp32" else inst.src_val
+    return oracle.fmm(F, inst.h, inst.src_idx, val)
+
+
+def assert_parity(got, ref, tol):
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(got)), "reachability differs"
+    if not fin.any():
+        return 0.0
+    scale = float(np.max(np.abs(ref[fin])))
+    err = float(np.max(np.abs(got[fin] - ref[fin])))
+    assert err <= tol * max(scale, 1e-30), (err, scale, err / max(scale, 1e-30))
+    return err / max(scale, 1e-30)
+
+
+# ------------------------------------------------------------------ workloads
+def test_point_source_2d_128():
+    inst = W.point_source_2d(128, (64, 64))
+    for dt, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        got, st = gpu_solve(inst, dt)
+        assert_parity(got, oracle_phi(inst, dt), tol)
+    # axis exactness survives in FP32 to rounding: phi(64+k, 64) = k h
+    got, _ = gpu_solve(inst, "fp32")
+    k = np.arange(64)
+    assert np.allclose(got[64, 64:], k * inst.h, rtol=2e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("tile", ["8x8x8", "4x4x4", "8x8x4", "8x4x4"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp64"])
+def test_oscillating_3d_small(tile, dtype):
+    inst = W.oscillating_3d(45)          # several tiles and a ragged tail for every tile shape
+    got, st = gpu_solve(inst, dtype, tile=tile)
+    assert_parity(got, oracle_phi(inst, dtype), TOL32 if dtype == "fp32" else TOL64)
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "fp64"])
+def test_maze_small(dtype):
+    inst = W.maze_3d(72, seed=3, n_slabs=4, gap=12)
+    got, st = gpu_solve(inst, dtype)
+    assert_parity(got, oracle_phi(inst, dtype), TOL32 if dtype == "fp32" else TOL64)
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "hostloop"])
+def test_schedules_agree(schedule):
+    inst = W.maze_3d(48, seed=7, n_slabs=3, gap=10, n_src=3)
+    got, st = gpu_solve(inst, "fp64", schedule=schedule)
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_small_grids(seed):
+    inst = W.random_small(seed, max_edge=21, p_barrier=0.08 if seed % 2 else 0.0)
+    for dt, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        got, _ = gpu_solve(inst, dt)
+        assert_parity(got, oracle_phi(inst, dt), tol)
+
+
+@pytest.mark.parametrize("ex", [1, 2, 3, 5])
+def test_paper_examples_2d(ex):
+    inst = W.paper_example_2d(ex, n=150)
+    for dt, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        got, _ = gpu_solve(inst, dt)
+        assert_parity(got, oracle_phi(inst, dt), tol)
+
+
+def test_lognormal_single_instance():
+    inst = W.lognormal_batch(B=2, seed=4, lo=40, hi=70)[1]
+    got, _ = gpu_solve(inst, "fp32")
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 9), (17, 1, 1), (1, 13, 1), (9, 9, 1), (3, 5, 7),
+                                  (8, 8, 8), (9, 8, 8), (16, 16, 17)])
+def test_odd_shapes_and_lines(dims):
+    inst = W.random_small(31, dims=dims, three_d=dims[2] > 1)
+    got, _ = gpu_solve(inst, "fp64")
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+
+
+def test_no_sources_gives_all_inf():
+    inst = W.random_small(5, dims=(10, 9, 8), three_d=True)
+    inst.src_idx = np.zeros(0, dtype=np.int64)
+    inst.src_val = np.zeros(0)
+    got, _ = gpu_solve(inst, "fp32")
+    assert np.all(np.isinf(got))
+
+
+def test_barrier_wall_and_hole():
+    F = np.ones((1, 20, 20))
+    F[0, :, 9] = 0.0
+    inst = W.Instance("wall", F, 0.1, np.array([0], np.int64), np.zeros(1))
+    got, _ = gpu_solve(inst, "fp32")
+    assert np.all(np.isinf(got[0, :, 9:]))
+    F[0, 19, 9] = 1.0
+    got, _ = gpu_solve(inst, "fp64")
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+
+
+def test_duplicate_sources_and_source_on_barrier():
+    F = np.ones((6, 7, 8))
+    F[2, 3, 4] = 0.0
+    idx = np.array([(2 * 7 + 3) * 8 + 4, 5, 5], dtype=np.int64)
+    val = np.array([0.0, 0.3, 0.1])
+    inst = W.Instance("dup", F, 0.2, idx, val)
+    got, _ = gpu_solve(inst, "fp64")
+    assert got.reshape(-1)[5] == 0.1
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+
+
+def test_source_out_of_range_is_an_error():
+    torch = _torch()
+    from paper_2106_15869_b300 import api, EikonalError
+    F = torch.ones(4, 5, 6, device="cuda")
+    with pytest.raises(EikonalError) as e:
+        api.solve(F, [0, 4 * 5 * 6], 0.1, return_stats=True)
+    assert e.value.code == 1
+
+
+def test_iteration_cap_reports_noconverge_and_upper_bounds():
+    torch = _torch()
+    from paper_2106_15869_b300 import api, EikonalError
+    inst = W.oscillating_3d(40)
+    F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
+    with pytest.raises(EikonalError) as e:
+        api.solve(F, inst.src_idx, inst.h, return_stats=True, max_iters=3)
+    assert e.value.code == 2
+    phi = api.solve(F, inst.src_idx, inst.h, max_iters=3).cpu().double().numpy()
+    ref = oracle_phi(inst, "fp32")
+    assert np.all(phi >= ref - 1e-4 * ref[np.isfinite(ref)].max())     # iterates are upper bounds
+
+
+def test_host_tensor_round_trip():
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    inst = W.oscillating_3d(33)
+    phi = api.solve(torch.as_tensor(inst.F, dtype=torch.float32), inst.src_idx, inst.h)
+    assert phi.device.type == "cpu"
+    assert_parity(phi.double().numpy(), oracle_phi(inst, "fp32"), TOL32)
+
+
+def test_repeated_calls_reuse_workspace():
+    inst = W.maze_3d(40, seed=11, n_slabs=3, gap=8)
+    a, _ = gpu_solve(inst, "fp32")
+    b, _ = gpu_solve(inst, "fp32")
+    ref = oracle_phi(inst, "fp32")
+    assert_parity(a, ref, TOL32)
+    assert_parity(b, ref, TOL32)
+
+
+# ------------------------------------------------------------------ remedy ablation
+def test_skip_remedy_breaks_parity_where_remedy_is_needed():
+    """Sec. 4.2: after Step 2 alone some values are wrong on multi-source /
+    variable-speed inputs; Step 3 finds and fixes them."""
+    inst = W.maze_3d(64, seed=3, n_slabs=5, gap=10, n_src=4)
+    ref = oracle_phi(inst, "fp64")
+    full, st = gpu_solve(inst, "fp64")
+    assert_parity(full, ref, TOL64)
+    assert st["tiles_flagged"] > 0
+    upd, st0 = gpu_solve(inst, "fp64", skip_remedy=True)
+    fin = np.isfinite(ref)
+    err = np.max(np.abs(upd[fin] - ref[fin])) / ref[fin].max()
+    assert err > 1e-3, err
+    assert np.all(upd[fin] >= ref[fin] - 1e-12)       # Step-2 values are upper bounds
+
+
+# ------------------------------------------------------------------ batched
+def test_batched_uneven_instances():
+    from paper_2106_15869_b300 import api
+    torch = _torch()
+    insts = W.lognormal_batch(B=5, seed=21, lo=20, hi=48) + [W.random_small(3, dims=(13, 7, 5), three_d=True)]
+    probs = [(torch.as_tensor(i.F, dtype=torch.float32).cuda(), i.src_idx, i.h, i.src_val) for i in insts]
+    outs, st = api.solve_batched(probs, return_stats=True)
+    assert st["status"] == 0
+    for i, o in zip(insts, outs):
+        assert_parity(o.cpu().double().numpy(), oracle_phi(i, "fp32"), TOL32)
+
+
+def test_batched_shared_speed_many_sources():
+    from paper_2106_15869_b300 import api
+    torch = _torch()
+    t = W.tomography_3d(40, rec_count=4, src_lattice=(5, 20, 35))
+    F = 1.0 / t["s_true"]
+    Ft = torch.as_tensor(F, dtype=torch.float64).cuda()
+    probs = [(Ft, [s], t["h"]) for s in t["sources"]]
+    outs = api.solve_batched(probs, shared_F=True)
+    for s, o in zip(t["sources"], outs):
+        ref = oracle.fmm(F, t["h"], [s])
+        assert_parity(o.cpu().numpy(), ref, TOL64)
+
+
+# ------------------------------------------------------------------ full-size workloads
+def test_full_point_source_2d_128_config():
+    inst = W.point_source_2d(128, (64, 64))
+    got, _ = gpu_solve(inst, "fp32")
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
+def test_full_oscillating_256_fp32():
+    """The 256^3 oscillating-speed workload at full size, all nodes vs the oracle."""
+    inst = W.oscillating_3d(256)
+    got, st = gpu_solve(inst, "fp32")
+    err = assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+    print("oscillating_3d_256 max rel err", err, st)
