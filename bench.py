@@ -198,13 +198,13 @@ def run_ours(args, ws, rank, local):
 
         def step(stats=True):
             return api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp,
-                             out=phi, return_stats=stats, order=args.order)
+                             out=phi, return_stats=stats, order=args.order, converge=args.converge)
     else:
         probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h, i.src_val) for i in insts]
 
         def step(stats=True):
             return api.solve_batched(probs, tile=args.tile, schedule=args.schedule, workspace=wsp,
-                                     return_stats=stats, order=args.order)
+                                     return_stats=stats, order=args.order, converge=args.converge)
 
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     for _ in range(args.warmup):
@@ -254,7 +254,7 @@ def run_ours(args, ws, rank, local):
             idx.copy_(idx_h, non_blocking=True)
             val.copy_(val_h, non_blocking=True)
             api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp, out=phi,
-                      order=args.order)
+                      order=args.order, converge=args.converge)
             phi_h.copy_(phi, non_blocking=True)
             ev1.record(stream)
             ev1.synchronize()
@@ -281,6 +281,7 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "nodes_per_gpu": n_nodes, "instances": len(insts),
                        "tile": args.tile, "schedule": args.schedule, "order": args.order,
+                       "converge": args.converge,
                        "l2": "flushed between steps (256 MiB write outside the per-step events)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
@@ -315,6 +316,7 @@ def main():
                     choices=["oscillating_256", "point_source_128", "maze_512", "lognormal_batch64"])
     ap.add_argument("--tile", default="auto")
     ap.add_argument("--schedule", default="auto")
+    ap.add_argument("--converge", default="auto", choices=["auto", "confirm", "sweep"])
     ap.add_argument("--order", type=float, default=0.0,
                     help="list order: 0 default bucketed, >0 bucket width, <0 unordered")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -67,6 +67,17 @@ extern "C" {
 #define EIK_SCHED_AUTO 0
 #define EIK_SCHED_PERSISTENT 1 /* one cooperative launch, bounded grid barriers */
 #define EIK_SCHED_HOSTLOOP 2   /* one launch per iteration, host reads the list size (synchronising) */
+#define EIK_SCHED_ASYNC 3      /* one cooperative launch, device work queue, no per-iteration barrier */
+
+/* Step-2 convergence test of an Active tile (Algorithm 2 moves a point to
+ * Source when its recomputation no longer changes it):
+ *   CONFIRM  a visit that changes nothing (the tile is visited again after
+ *            any visit that changed it, in a later iteration)
+ *   SWEEP    the relaxation inside a visit ends with a sweep that changes
+ *            nothing (the same test, taken at sweep granularity) */
+#define EIK_CONVERGE_AUTO 0
+#define EIK_CONVERGE_CONFIRM 1
+#define EIK_CONVERGE_SWEEP 2
 
 /* precision */
 #define EIK_FP32 0
@@ -80,7 +91,7 @@ typedef struct {
 
 /* per-call options; a zero-filled struct (or NULL) selects the defaults */
 typedef struct {
-    int32_t tile;         /* EIK_TILE_* (0 = auto: 8x8x1 for 2D, else 4x4x4) */
+    int32_t tile;         /* EIK_TILE_* (0 = auto: 16x16x1 for 2D, else 8x8x4) */
     int32_t schedule;     /* EIK_SCHED_* (0 = auto: persistent when co-residency allows) */
     int64_t max_iters;    /* cap per loop (update, remedy); 0 = automatic */
     int32_t precision;    /* EIK_FP32 / EIK_FP64 */
@@ -88,7 +99,8 @@ typedef struct {
     float order;          /* list order: 0 = default (bucketed, width 4), > 0 = bucket width in
                              tile-crossing times, < 0 = unordered (every listed tile visited in
                              every iteration, the schedule of Algorithm 2 as printed) */
-    int32_t reserved[3];  /* must be 0 */
+    int32_t converge;     /* Step-2 convergence test of a tile (EIK_CONVERGE_*) */
+    int32_t reserved[2];  /* must be 0 */
 } eik_options;
 
 /* run statistics (filled when a stats pointer is passed; the call then synchronises) */

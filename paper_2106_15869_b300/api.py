@@ -75,8 +75,8 @@ def _workspace(device, nbytes, ws: Workspace | None):
 
 
 def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", schedule="auto",
-          skip_remedy=False, max_iters=0, order=0.0, return_stats=False, workspace: Workspace | None = None,
-          out: torch.Tensor | None = None):
+          skip_remedy=False, max_iters=0, order=0.0, converge="auto", return_stats=False,
+          workspace: Workspace | None = None, out: torch.Tensor | None = None):
     """Arrival times phi of ||grad phi|| = 1/F with fixed values at the sources.
 
     F: (ny, nx) or (nz, ny, nx) float32 (or float64 = FP64 validation mode)
@@ -97,7 +97,7 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     val = _as_values(src_val, idx.numel(), Fd.dtype, dev)
     lib = _lib.load()
     g = _lib.grids_array([(nx, ny, nz, h)])
-    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order)
+    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge)
     nbytes = lib.eik_workspace_size(g, ctypes.byref(opt))
     if nbytes == 0:
         raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grid or options")
@@ -116,7 +116,7 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
 
 
 def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, max_iters=0, order=0.0,
-                  return_stats=False, workspace: Workspace | None = None, shared_F: bool = False):
+                  converge="auto", return_stats=False, workspace: Workspace | None = None, shared_F: bool = False):
     """Solve many independent grids in one set of launches.
 
     problems: list of (F, src_idx, h) or (F, src_idx, h, src_val); all F on the
@@ -158,7 +158,7 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
     src_val = torch.cat(vals) if sum(nsrc) else torch.zeros(0, dtype=dtype, device=dev)
     lib = _lib.load()
     g = _lib.grids_array(dims)
-    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order)
+    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge)
     B = len(problems)
     nbytes = lib.eik_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:

@@ -11,7 +11,8 @@
 
 #include "../../include/eikonal.h"
 #include "eik_common.cuh"
-#include "eik_forward.cuh"
+#include "eik_kernels.cuh"
+#include "eik_async.cuh"
 
 using namespace eik;
 
@@ -58,7 +59,7 @@ TileShape tile_shape(int tile) {
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Opts {
-    int tile, schedule, precision, skip_remedy;
+    int tile, schedule, precision, skip_remedy, converge;
     long long max_iters;
     float order;           // <= 0: unordered lists (every listed tile visited each iteration)
 };
@@ -74,16 +75,19 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
     const float ord = o ? o->order : 0.0f;
     if (!(ord == ord)) return false;                       // NaN
     out.order = ord == 0.0f ? kDefaultOrder : (ord < 0.0f ? 0.0f : ord);
+    out.converge = o ? o->converge : EIK_CONVERGE_AUTO;
+    if (out.converge < 0 || out.converge > EIK_CONVERGE_SWEEP) return false;
+    if (out.converge == EIK_CONVERGE_AUTO) out.converge = EIK_CONVERGE_CONFIRM;
     if (o) {
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 2; ++q)
             if (o->reserved[q] != 0) return false;
     }
     if (out.precision != EIK_FP32 && out.precision != EIK_FP64) return false;
-    if (out.schedule < 0 || out.schedule > EIK_SCHED_HOSTLOOP) return false;
+    if (out.schedule < 0 || out.schedule > EIK_SCHED_ASYNC) return false;
     if (out.tile < 0 || out.tile > EIK_TILE_8x8x1) return false;
     bool all2d = true;
     for (int64_t b = 0; b < B; ++b) all2d = all2d && grids[b].nz == 1;
-    if (out.tile == EIK_TILE_AUTO) out.tile = all2d ? EIK_TILE_8x8x1 : EIK_TILE_4x4x4;
+    if (out.tile == EIK_TILE_AUTO) out.tile = all2d ? EIK_TILE_16x16x1 : EIK_TILE_8x8x4;
     if ((out.tile == EIK_TILE_16x16x1 || out.tile == EIK_TILE_8x8x1) && !all2d) return false;
     if (out.max_iters < 0) return false;
     return true;
@@ -91,8 +95,10 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
 
 // workspace regions (byte offsets), all 256-byte aligned
 struct Layout {
-    size_t ctl, desc, inst_acc, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t, total;
+    size_t ctl, desc, inst_acc, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t;
+    size_t q_data, q_seq, q_state, total;
     long long n_tiles;
+    unsigned long long q_slots;
     std::vector<InstDesc> desc_host;
 };
 
@@ -131,10 +137,10 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
     L.ctl = take(sizeof(Ctl));
     L.desc = take(sizeof(InstDesc) * (size_t)B);
-    L.inst_acc = take(2 * sizeof(double) * (size_t)B);
+    L.inst_acc = take(4 * sizeof(double) * (size_t)B);
     L.inst_scale = take(sizeof(float) * (size_t)B);
     L.tile_inst = take(4 * (size_t)tiles);
-    L.tile_nb = take(4 * 6 * (size_t)tiles);
+    L.tile_nb = take(4 * 8 * (size_t)tiles);
     L.tstate = take(4 * (size_t)tiles);
     L.tstamp = take(4 * (size_t)tiles);
     L.tkey = take(2 * 4 * (size_t)tiles);
@@ -142,6 +148,16 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     L.list1 = take(4 * (size_t)tiles);
     L.phi_t = take(esz * (size_t)(tiles * V));
     L.tau_t = take(esz * (size_t)(tiles * V));
+    // work queue of the asynchronous schedule: 2^k slots > tiles + any number of warps
+    // (only when that schedule may run: explicitly requested, or chosen by auto)
+    unsigned long long q = 1;
+    const bool need_q = o.schedule == EIK_SCHED_ASYNC || o.schedule == EIK_SCHED_AUTO;
+    if (need_q)
+        while (q < 2ull * (unsigned long long)tiles + 65536ull) q <<= 1;
+    L.q_slots = need_q ? q : 0;
+    L.q_data = take(4 * (size_t)L.q_slots);
+    L.q_seq = take(8 * (size_t)L.q_slots);
+    L.q_state = take(need_q ? 4 * (size_t)tiles : 0);
     L.total = off;
     return true;
 }
@@ -249,6 +265,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     P.max_iters = o.max_iters > 0 ? o.max_iters : auto_max_iters(L);
     P.skip_remedy = o.skip_remedy;
+    P.one_visit = o.converge == EIK_CONVERGE_SWEEP ? 1 : 0;
     P.max_sweeps = 4 * (BX + BY + BZ) + 8;
     P.F = static_cast<const T *>(F);
     P.src_idx = reinterpret_cast<const long long *>(src_idx);
@@ -269,6 +286,9 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     if (P.ordered) {
         k_scale<BX, BY, BZ><<<(P.B + 127) / 128, 128, 0, st>>>(P.desc, P.inst_acc, P.inst_scale, P.B, P.order);
         EIK_CUDA(cudaGetLastError(), "k_scale launch");
+        k_tile_scale<<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P.tile_nb, P.inst_scale,
+                                                                                               (int)L.n_tiles);
+        EIK_CUDA(cudaGetLastError(), "k_tile_scale launch");
     }
     if (n_src > 0) {
         k_sources<T, BX, BY, BZ><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(P);
@@ -287,7 +307,28 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
 
     bool done = false;
     pe.record(1, st);
-    if (sched == EIK_SCHED_PERSISTENT) {
+    if (sched == EIK_SCHED_ASYNC) {
+        AsyncQ Q;
+        Q.data = reinterpret_cast<int *>(ws + L.q_data);
+        Q.seq = reinterpret_cast<unsigned long long *>(ws + L.q_seq);
+        Q.qstate = reinterpret_cast<int *>(ws + L.q_state);
+        Q.mask = L.q_slots - 1;
+        Q.visit_cap = P.max_iters * (long long)L.n_tiles;
+        int per_sm_a = 0;
+        EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_async<T, BX, BY, BZ>, CTA, 0),
+                 "occupancy query");
+        if (!di.coop || per_sm_a < 1) return fail(EIK_ERR_CUDA, "the asynchronous schedule needs a cooperative launch");
+        k_queue_init<<<std::min<unsigned long long>((L.q_slots + 255) / 256, 4096), 256, 0, st>>>(Q, (int)L.n_tiles);
+        EIK_CUDA(cudaGetLastError(), "k_queue_init launch");
+        k_queue_seed<<<std::max(1, std::min((int)((L.n_tiles + 255) / 256), 1024)), 256, 0, st>>>(Q, P.ctl, P.list0);
+        EIK_CUDA(cudaGetLastError(), "k_queue_seed launch");
+        const int grid = per_sm_a * di.sms;
+        void *args[] = {&P, &Q};
+        EIK_CUDA(cudaLaunchCooperativeKernel((const void *)k_async<T, BX, BY, BZ>, dim3(grid), dim3(CTA), args, 0, st),
+                 "cooperative launch");
+        done = true;
+    }
+    if (!done && sched == EIK_SCHED_PERSISTENT) {
         int grid = per_sm * di.sms;
         const int need = (int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
         if (grid > need) grid = need;
@@ -307,14 +348,16 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         // host loop: one launch per iteration, the list size is read back each time
         const int grid_cap = std::max(1, per_sm * di.sms);
         Ctl *dctl = P.ctl;
-        int n = 0;
+        int n = 0, prev_n = 0;
         EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
         EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
         long long it = 0, r = 0;
         bool capped = false;
         while (n > 0) {
             if (it >= P.max_iters) { capped = true; break; }
-            k_update_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(P, (int)it);
+            k_update_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(
+                P, (int)it, prev_n);
+            prev_n = n;
             EIK_CUDA(cudaGetLastError(), "k_update_iter launch");
             ++it;
             EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[it % 3], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
@@ -324,10 +367,15 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
             k_detect<T, BX, BY, BZ><<<std::min((int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta), grid_cap), CTA, 0, st>>>(P);
             EIK_CUDA(cudaGetLastError(), "k_detect launch");
             EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+            const int zeros[4] = {0, 0, 0, 0};
+            EIK_CUDA(cudaMemcpyAsync(&dctl->nproc[0], zeros, sizeof(zeros), cudaMemcpyHostToDevice, st), "nproc reset");
             EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+            prev_n = 0;
             while (n > 0) {
                 if (r >= P.max_iters) { capped = true; break; }
-                k_remedy_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(P, (int)r);
+                k_remedy_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(
+                    P, (int)r, prev_n);
+                prev_n = n;
                 EIK_CUDA(cudaGetLastError(), "k_remedy_iter launch");
                 ++r;
                 EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[r % 3], sizeof(int), cudaMemcpyDeviceToHost, st),

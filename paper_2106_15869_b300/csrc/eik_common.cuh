@@ -55,9 +55,14 @@ struct Ctl {
     int rcnt[3];                  // Step-3 list sizes
     unsigned kmin[3];             // Step-2 smallest key listed for iteration it (slot it % 3)
     unsigned rkmin[3];            // Step-3 smallest key listed for iteration r
+    int nproc[4];                 // tiles visited (not deferred) in iteration it (slot it % 4)
+    float win[2];                 // bucket width of the host-loop schedule, by iteration parity
     long long iters_update, iters_remedy;
     long long tiles_update, tiles_flagged, tiles_remedy, sweeps, tiles_deferred;
-    long long pad1[2];
+    unsigned long long q_head, q_tail;   // work-queue positions (asynchronous schedule)
+    int q_pending;                       // tiles queued or being visited in the current phase
+    int q_stop;                          // the visit cap was reached: every warp leaves the phase
+    long long q_visits;                  // visits in the current phase (cap check)
 };
 static_assert(sizeof(Ctl) <= 256, "the control block is zeroed by 64 threads");
 
@@ -70,6 +75,11 @@ __device__ __forceinline__ float key_dec(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 constexpr unsigned kKeyInf = 0xff800000u;   // key_enc(+inf)
+
+// Encoded key of value v for an instance with key scale sc (1/delta).  A
+// scale of 0 marks an instance that is not ordered: all its keys are 0, so
+// its listed tiles are always inside the window.
+__device__ __forceinline__ unsigned scaled_key(float v, float sc) { return key_enc(sc > 0.0f ? v * sc : 0.0f); }
 
 // ----------------------------------------------------------------- helpers
 template <class T> struct Num;
@@ -101,6 +111,23 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ unsigned ld_volatile_u(const unsigned *p) { return *(const volatile unsigned *)p; }
+// Bucket width of the ordered schedule for the next iteration (the same in
+// every CTA).  It doubles while an iteration visits less than 1/16 of its
+// list and fewer tiles than half the thread groups of the launch (most of the
+// list waits, and the GPU would idle: keys spread over many buckets, e.g.
+// behind slow walls), and halves back toward one unit once more than half of
+// a list is visited.  Widths are in key units (order * tile-crossing times).
+__device__ __forceinline__ float adapt_window(float w, int visited, int listed, int groups, int warps) {
+    (void)warps;
+    if (listed <= 0) return w;
+    if (16 * visited < listed && 2 * visited < groups) w *= 2.0f;
+    else if (2 * visited > listed) w = fmaxf(1.0f, 0.5f * w);
+    return fminf(w, 1e30f);
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // Exact root of eq. (6) given the per-axis upwind minima and tau = h/F:
 //   sum_d ((u - a_d)^+)^2 = tau^2, a1 <= a2 <= a3 sorted.

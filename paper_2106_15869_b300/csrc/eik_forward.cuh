@@ -38,7 +38,8 @@ struct FwdParams {
     int B;
     int n_tiles;                 // total tiles over all instances
     int *tile_inst;
-    int *tile_nb;                // [n_tiles][6] neighbour tile ids (-1 outside)
+    int *tile_nb;                // [n_tiles][8]: neighbour tile ids (-1 outside) across -x,+x,-y,+y,-z,+z,
+                                 // the instance, and (ordered schedule) the instance's key scale
     int *tstate;
     int *tstamp;
     unsigned *tkey;              // [2][n_tiles] encoded list keys (ordered schedule)
@@ -51,6 +52,7 @@ struct FwdParams {
     Ctl *ctl;
     long long max_iters;
     int skip_remedy;
+    int one_visit;               // Step 2: a visit whose relaxation converged moves the tile to Source
     int max_sweeps;              // cap on in-tile sweeps per visit
     const T *F;                  // packed input speeds
     const long long *src_idx;
@@ -246,8 +248,10 @@ __device__ __forceinline__ int warps_total() { return gridDim.x * kWarpsPerCta; 
 // 1/delta of its instance, delta = order * (tile edge) * h / mean(F), i.e.
 // `order` tile-crossing times.  An iteration visits the listed tiles whose
 // key lies within one bucket of the smallest key in the list and defers the
-// others to the next list unvisited.  The sets and their rules are those of
-// Algorithm 2; only the iteration in which a listed tile is visited changes,
+// others to the next list unvisited.  The bucket width starts at one unit and adapts
+// (adapt_window) when most of a list is deferred.  The sets and their rules
+// are those of Algorithm 2; only the iteration in which a listed tile is
+// visited changes,
 // and the fixed point reached does not depend on that (the discrete solution
 // is unique).  Keys live in two parities: pushes for iteration it+1 write
 // tkey[(it+1)&1], the visit in iteration it reads and clears tkey[it&1].
@@ -257,11 +261,11 @@ struct OrderCtx {
     float theta;        // visit iff key < theta (or every key is +inf)
 };
 
-__device__ __forceinline__ OrderCtx order_begin(bool on, unsigned kmin) {
+__device__ __forceinline__ OrderCtx order_begin(bool on, unsigned kmin, float width) {
     OrderCtx o;
     o.on = on;
     o.kmin = on ? kmin : kKeyInf;
-    o.theta = key_dec(o.kmin) + 1.0f;
+    o.theta = key_dec(o.kmin) + width;
     return o;
 }
 
@@ -286,7 +290,8 @@ __device__ __forceinline__ float face_min(unsigned sel, const T (&v)[TileGeom<BX
 // ---------------------------------------------------------------- Step 2
 // One pass over the Active list of iteration `it` (slot it % 3).
 template <class T, int BX, int BY, int BZ>
-__device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigned kmin_cur, long long &st_tiles,
+__device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigned kmin_cur, float width,
+                            int *s_visits, long long &st_tiles,
                             long long &st_sweeps, long long &st_def) {
     using G = TileGeom<BX, BY, BZ>;
     Ctl *ctl = P.ctl;
@@ -296,18 +301,17 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
     unsigned *kcur = P.tkey + (size_t)(it & 1) * P.n_tiles;
     unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
     const int lane = lane_id();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {   // slot (it+2)%3 was last read in iteration it-1
-        ctl->cnt[(it + 2) % 3] = 0;
-        ctl->kmin[(it + 2) % 3] = kKeyInf;
-    }
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur);
+    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);                       // n > n_tiles only after an overflow
     for (int idx = warp_global(); idx < n; idx += warps_total()) {
         const int g = __ldcg(in + idx);
-        unsigned key = kKeyInf;
+        // one round trip: the tile record (lanes 0-7) and its key (lane 8)
+        const int rec = lane < 8 ? __ldcg(P.tile_nb + 8 * g + lane) : (lane == 8 && ord.on ? (int)__ldcg(kcur + g) : -1);
+        const int nbf = lane < 6 ? rec : -1;
+        const float sc = __int_as_float(__shfl_sync(kFull, rec, 7));
+        unsigned key = (unsigned)__shfl_sync(kFull, rec, 8);
         if (ord.on) {
-            if (lane == 0) key = atomicExch(kcur + g, kKeyInf);
-            key = __shfl_sync(kFull, key, 0);
+            if (lane == 8) __stcg(kcur + g, kKeyInf);   // no one writes this parity in this iteration
             if (!order_visit(ord, key)) {        // deferred: listed again, not visited
                 if (lane == 0) {
                     atomicMin(knext + g, key);
@@ -317,15 +321,14 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
                 continue;
             }
         }
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 6 * g + lane) : -1;
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
         bool changed;
         const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
-        if (lane == 0) { st_tiles++; st_sweeps += s; }
-        if (changed) {
+        if (lane == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
+        if (changed && (!P.one_visit || s >= P.max_sweeps)) {
             // stays Active; its next visit confirms (or not) that it converged
             if (ord.on && lane == 0) atomicMin(knext + g, key);
             warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, lane == 0, g, ord.on ? &ctl->kmin[nslot] : nullptr, key);
@@ -336,14 +339,13 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
             unsigned kf = kKeyInf;
             if (ord.on) {
                 // key of the neighbour across face `lane`: the smallest value on that face
-                const float sc = P.inst_scale[__ldcg(P.tile_inst + g)];
                 float fm = __int_as_float(0x7f800000);
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
                     const unsigned k = __reduce_min_sync(kFull, key_enc(face_min<T, BX, BY, BZ>(~0u, v, f)));
                     if (lane == f) fm = key_dec(k);
                 }
-                kf = key_enc(fm * sc);
+                kf = scaled_key(fm, sc);
                 if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
             }
             warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, act, nbf, ord.on ? &ctl->kmin[nslot] : nullptr, kf);
@@ -362,7 +364,9 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
     Ctl *ctl = P.ctl;
     const int lane = lane_id();
     for (int g = warp_global(); g < P.n_tiles; g += warps_total()) {
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 6 * g + lane) : -1;
+        const int rec = lane < 8 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        const int nbf = lane < 6 ? rec : -1;
+        const float sc = __int_as_float(__shfl_sync(kFull, rec, 7));
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         bool low = false;
@@ -380,7 +384,7 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
         }
         const bool any = __any_sync(kFull, low);
         if (P.ordered) {
-            const unsigned k = warp_min_key(kmin * P.inst_scale[__ldcg(P.tile_inst + g)]);
+            const unsigned k = __reduce_min_sync(kFull, scaled_key(kmin, sc));
             if (lane == 0) {
                 __stcg(P.tkey + g, any ? k : kKeyInf);
                 __stcg(P.tkey + P.n_tiles + g, kKeyInf);
@@ -398,7 +402,8 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
 
 // One pass over the Remedy list of loop iteration r (slot r % 3, stamp r+1).
 template <class T, int BX, int BY, int BZ>
-__device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned kmin_cur, long long &st_tiles,
+__device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned kmin_cur, float width,
+                            int *s_visits, long long &st_tiles,
                             long long &st_sweeps, long long &st_def) {
     using G = TileGeom<BX, BY, BZ>;
     Ctl *ctl = P.ctl;
@@ -408,19 +413,17 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
     unsigned *kcur = P.tkey + (size_t)(r & 1) * P.n_tiles;
     unsigned *knext = P.tkey + (size_t)((r + 1) & 1) * P.n_tiles;
     const int lane = lane_id();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->rcnt[(r + 2) % 3] = 0;
-        ctl->rkmin[(r + 2) % 3] = kKeyInf;
-    }
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur);
+    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
     const int next_stamp = r + 2;
     for (int idx = warp_global(); idx < n; idx += warps_total()) {
         const int g = __ldcg(in + idx);
-        unsigned key = kKeyInf;
+        const int rec = lane < 8 ? __ldcg(P.tile_nb + 8 * g + lane) : (lane == 8 && ord.on ? (int)__ldcg(kcur + g) : -1);
+        const int nbf = lane < 6 ? rec : -1;
+        const float sc = __int_as_float(__shfl_sync(kFull, rec, 7));
+        unsigned key = (unsigned)__shfl_sync(kFull, rec, 8);
         if (ord.on) {
-            if (lane == 0) key = atomicExch(kcur + g, kKeyInf);
-            key = __shfl_sync(kFull, key, 0);
+            if (lane == 8) __stcg(kcur + g, kKeyInf);
             if (!order_visit(ord, key)) {        // deferred: listed again, not visited
                 bool want = false;
                 if (lane == 0) {
@@ -432,7 +435,6 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
                 continue;
             }
         }
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 6 * g + lane) : -1;
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
@@ -440,7 +442,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         const int fm = changed_faces<BX, BY, BZ>(mine);
-        if (lane == 0) { st_tiles++; st_sweeps += s; }
+        if (lane == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
         // The tile is relaxed to its local fixed point; a neighbour whose facing
         // boundary drops re-lists it.  Lanes 0-5 list the neighbour across face
         // `lane` when a node on that face dropped; lane 6 re-lists the tile
@@ -450,7 +452,6 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         if (lane == 6 && changed && s >= P.max_sweeps) cand = g;
         unsigned kc = kKeyInf;
         if (ord.on) {
-            const float sc = P.inst_scale[__ldcg(P.tile_inst + g)];
             float dm = __int_as_float(0x7f800000);
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
@@ -458,7 +459,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
                 const unsigned k = __reduce_min_sync(kFull, key_enc(face_min<T, BX, BY, BZ>(mine, v, f)));
                 if (lane == f) dm = key_dec(k);
             }
-            kc = lane == 6 ? key : key_enc(dm * sc);
+            kc = lane == 6 ? key : scaled_key(dm, sc);
             if (cand >= 0) atomicMin(knext + cand, kc);
         }
         const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
@@ -468,268 +469,6 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
         __syncwarp();
     }
-}
-
-// ---------------------------------------------------------------- kernels
-// Descriptor upload (by-value parameter, so that the call can be captured).
-__global__ void k_write_desc(InstDesc *desc, double *inst_acc, DescChunk chunk) {
-    const int i = threadIdx.x;
-    if (i < chunk.count) {
-        desc[chunk.first + i] = chunk.d[i];
-        inst_acc[2 * (chunk.first + i)] = 0.0;
-        inst_acc[2 * (chunk.first + i) + 1] = 0.0;
-    }
-}
-
-// 1/delta per instance for the ordered schedule: delta = order * (mean tile
-// edge) * h / mean(F over passable nodes).
-template <int BX, int BY, int BZ>
-__global__ void k_scale(const InstDesc *desc, const double *inst_acc, float *inst_scale, int B, float order) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
-    const double cnt = inst_acc[2 * b + 1], sum = inst_acc[2 * b];
-    const double meanF = cnt > 0 ? sum / cnt : 0.0;
-    double sc = meanF > 0 ? meanF / ((double)order * edge * desc[b].h) : 1.0;
-    if (!(sc > 0) || !(sc < 1e30)) sc = 1.0;
-    inst_scale[b] = (float)sc;
-}
-
-// Step 1a: bricked tau = h/F and phi = +inf; per-tile state and neighbour
-// ids; control block.  One CTA of V threads per tile.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_init(FwdParams<T> P) {
-    using G = TileGeom<BX, BY, BZ>;
-    __shared__ int s_b;
-    const int g = blockIdx.x;
-    if (threadIdx.x == 0) s_b = find_inst_by_tile(P.desc, P.B, g);
-    __syncthreads();
-    const InstDesc &d = P.desc[s_b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
-    const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    T tau = Num<T>::inf();
-    double fsum = 0.0, fcnt = 0.0;
-    if (i < d.nx && j < d.ny && k < d.nz) {
-        const T f = P.F[d.in_off + ((long long)k * d.ny + j) * d.nx + i];
-        if (f > T(0)) { tau = T(d.h) / f; fsum = (double)f; fcnt = 1.0; }
-    }
-    P.tau_t[(size_t)g * G::V + tid] = tau;
-    P.phi_t[(size_t)g * G::V + tid] = Num<T>::inf();
-    if (tid == 0) {
-        P.tile_inst[g] = s_b;
-        P.tstate[g] = kDistant;
-        P.tstamp[g] = 0;
-        P.tkey[g] = kKeyInf;
-        P.tkey[P.n_tiles + g] = kKeyInf;
-    }
-    if (P.ordered) {   // per-instance mean speed for the bucket width
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
-            fcnt += __shfl_xor_sync(0xffffffffu, fcnt, o);
-        }
-        if ((tid & 31) == 0 && fcnt > 0) {
-            atomicAdd(P.inst_acc + 2 * s_b, fsum);
-            atomicAdd(P.inst_acc + 2 * s_b + 1, fcnt);
-        }
-    }
-    if (tid < 6) {
-        int nb;
-        switch (tid) {
-            case 0: nb = tx > 0 ? g - 1 : -1; break;
-            case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
-            case 2: nb = ty > 0 ? g - d.tx : -1; break;
-            case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
-            case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
-            default: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
-        }
-        P.tile_nb[6 * g + tid] = nb;
-    }
-    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
-        const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
-        reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
-    }
-}
-
-__device__ __forceinline__ void atomic_min_val(float *p, float v) {
-    int old = __float_as_int(*(volatile float *)p);
-    while (v < __int_as_float(old)) {
-        const int prev = atomicCAS(reinterpret_cast<int *>(p), old, __float_as_int(v));
-        if (prev == old) break;
-        old = prev;
-    }
-}
-__device__ __forceinline__ void atomic_min_val(double *p, double v) {
-    unsigned long long old = __double_as_longlong(*(volatile double *)p);
-    while (v < __longlong_as_double(old)) {
-        const unsigned long long prev =
-            atomicCAS(reinterpret_cast<unsigned long long *>(p), old, (unsigned long long)__double_as_longlong(v));
-        if (prev == old) break;
-        old = prev;
-    }
-}
-
-// Step 1b: sources fixed (phi = value, tau = -1 marker); Active = the tiles
-// that hold the sources' face neighbours (the source tile and, for a source on
-// a tile face, the tile across that face).
-template <class T, int BX, int BY, int BZ>
-__global__ void k_sources(FwdParams<T> P) {
-    using G = TileGeom<BX, BY, BZ>;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= P.n_src) return;
-    const int b = find_inst_by_src(P.desc, P.B, s);
-    const InstDesc &d = P.desc[b];
-    if (s < d.src_begin || s >= d.src_end) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
-    const long long p = P.src_idx[s];
-    const long long N = (long long)d.nx * d.ny * d.nz;
-    if (p < 0 || p >= N) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
-    const int i = (int)(p % d.nx), j = (int)((p / d.nx) % d.ny), k = (int)(p / ((long long)d.nx * d.ny));
-    const int tx = i / BX, ty = j / BY, tz = k / BZ;
-    const int g = (int)(d.tile_base + ((long long)tz * d.ty + ty) * d.tx + tx);
-    const int loc = ((k % BZ) * BY + (j % BY)) * BX + (i % BX);
-    atomic_min_val(P.phi_t + (size_t)g * G::V + loc, P.src_val[s]);
-    P.tau_t[(size_t)g * G::V + loc] = T(-1);
-    int cand[7];
-    int nc = 0;
-    cand[nc++] = g;
-    if (i % BX == 0 && i > 0) cand[nc++] = g - 1;
-    if (i % BX == BX - 1 && i + 1 < d.nx) cand[nc++] = g + 1;
-    if (j % BY == 0 && j > 0) cand[nc++] = g - d.tx;
-    if (j % BY == BY - 1 && j + 1 < d.ny) cand[nc++] = g + d.tx;
-    if (k % BZ == 0 && k > 0) cand[nc++] = g - d.tx * d.ty;
-    if (k % BZ == BZ - 1 && k + 1 < d.nz) cand[nc++] = g + d.tx * d.ty;
-    const unsigned key = key_enc((float)P.src_val[s] * P.inst_scale[b]);
-    for (int q = 0; q < nc; ++q) {
-        if (P.ordered) {
-            atomicMin(P.tkey + cand[q], key);
-            atomicMin(&P.ctl->kmin[0], key);
-        }
-        if (atomicCAS(P.tstate + cand[q], (int)kDistant, (int)kActive) == (int)kDistant) {
-            const int pos = atomicAdd(&P.ctl->cnt[0], 1);
-            if (pos < P.n_tiles) P.list0[pos] = cand[q];
-            else atomicOr(&P.ctl->flags, kFlagOverflow);
-        }
-    }
-}
-
-template <class T>
-__device__ __forceinline__ void flush_stats(const FwdParams<T> &P, long long a, long long b, long long c,
-                                            long long d, long long e) {
-    if (lane_id() == 0) {
-        if (e) atomicAdd((unsigned long long *)&P.ctl->tiles_deferred, (unsigned long long)e);
-        if (a) atomicAdd((unsigned long long *)&P.ctl->tiles_update, (unsigned long long)a);
-        if (b) atomicAdd((unsigned long long *)&P.ctl->tiles_flagged, (unsigned long long)b);
-        if (c) atomicAdd((unsigned long long *)&P.ctl->tiles_remedy, (unsigned long long)c);
-        if (d) atomicAdd((unsigned long long *)&P.ctl->sweeps, (unsigned long long)d);
-    }
-}
-
-// resident CTAs per SM asked of the compiler (register budget per thread =
-// 65536 / (32 * kWarpsPerCta * this)): more warps in flight for small tiles
-template <class T, int BX, int BY, int BZ>
-constexpr int min_ctas() {
-    return sizeof(T) == 8 ? 2   // FP64 validation mode: registers over occupancy
-           : TileGeom<BX, BY, BZ>::NPL <= 2 ? 6 : TileGeom<BX, BY, BZ>::NPL <= 4 ? 5
-           : TileGeom<BX, BY, BZ>::NPL <= 8 ? 3 : 2;
-}
-
-template <class T, int BX, int BY, int BZ>
-struct WarpSmem {
-    T phi[kWarpsPerCta][TileGeom<BX, BY, BZ>::S];
-};
-
-// Steps 2 and 3 in one cooperative launch; iterations are separated by the
-// bounded grid barrier.  Every warp reads the same list size after a
-// barrier, so all CTAs leave the loops together.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_persistent(FwdParams<T> P) {
-    __shared__ WarpSmem<T, BX, BY, BZ> sm;
-    __shared__ int s_n;
-    __shared__ unsigned s_k;
-    T *my = sm.phi[warp_in_cta()];
-    init_stage<T, BX, BY, BZ>(my);
-    Ctl *ctl = P.ctl;
-    unsigned long long target = 0;
-    long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0, deferred = 0;
-    int it = 0, r = 0;
-    for (;; ++it) {
-        if (threadIdx.x == 0) { s_n = ld_volatile(&ctl->cnt[it % 3]); s_k = ld_volatile_u(&ctl->kmin[it % 3]); }
-        __syncthreads();
-        const int n = s_n;
-        const unsigned kq = s_k;
-        if (n == 0) break;
-        if (it >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
-        update_pass<T, BX, BY, BZ>(P, my, it, n, kq, t_upd, sweeps, deferred);
-        if (!grid_sync(ctl, target)) goto done;
-    }
-    if (P.skip_remedy) goto done;
-    detect_pass<T, BX, BY, BZ>(P, my, t_flag);
-    if (!grid_sync(ctl, target)) goto done;
-    for (;; ++r) {
-        if (threadIdx.x == 0) { s_n = ld_volatile(&ctl->rcnt[r % 3]); s_k = ld_volatile_u(&ctl->rkmin[r % 3]); }
-        __syncthreads();
-        const int n = s_n;
-        const unsigned kq = s_k;
-        if (n == 0) break;
-        if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
-        remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, t_rem, sweeps, deferred);
-        if (!grid_sync(ctl, target)) goto done;
-    }
-done:
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->iters_update = it;
-        ctl->iters_remedy = r;
-    }
-    flush_stats<T>(P, t_upd, t_flag, t_rem, sweeps, deferred);
-}
-
-// Host-loop schedule: one launch per iteration.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_update_iter(FwdParams<T> P, int it) {
-    __shared__ WarpSmem<T, BX, BY, BZ> sm;
-    const int n = ld_volatile(&P.ctl->cnt[it % 3]);
-    const unsigned kq = ld_volatile_u(&P.ctl->kmin[it % 3]);
-    long long t = 0, s = 0, d = 0;
-    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
-    update_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], it, n, kq, t, s, d);
-    flush_stats<T>(P, t, 0, 0, s, d);
-}
-
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_detect(FwdParams<T> P) {
-    __shared__ WarpSmem<T, BX, BY, BZ> sm;
-    long long f = 0;
-    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
-    detect_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], f);
-    flush_stats<T>(P, 0, f, 0, 0, 0);
-}
-
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_remedy_iter(FwdParams<T> P, int r) {
-    __shared__ WarpSmem<T, BX, BY, BZ> sm;
-    const int n = ld_volatile(&P.ctl->rcnt[r % 3]);
-    const unsigned kq = ld_volatile_u(&P.ctl->rkmin[r % 3]);
-    long long t = 0, s = 0, d = 0;
-    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
-    remedy_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], r, n, kq, t, s, d);
-    flush_stats<T>(P, 0, 0, t, s, d);
-}
-
-// Output: bricked phi -> caller's row-major phi.  One CTA of V threads per tile.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_unpack(FwdParams<T> P) {
-    using G = TileGeom<BX, BY, BZ>;
-    const int g = blockIdx.x;
-    const int b = P.tile_inst[g];
-    const InstDesc &d = P.desc[b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
-    const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    if (i < d.nx && j < d.ny && k < d.nz)
-        P.phi_out[d.out_off + ((long long)k * d.ny + j) * d.nx + i] = P.phi_t[(size_t)g * G::V + tid];
 }
 
 }  // namespace eik

@@ -1,0 +1,265 @@
+// eik_group.cuh -- latency mode of the tile passes: a group of threads per tile.
+//
+// In an iteration with a short list (the usual case in Step 2, where the
+// Active set is a thin band) the iteration time is the latency of one tile
+// visit, not throughput.  There, a group of GT threads (GT = min(V, CTA))
+// owns a tile with one node per thread (two for 512-node tiles), so a sweep
+// costs one local solve plus a named barrier instead of V/32 solves in a row;
+// the group's OR-barrier is the convergence flag.  The rules applied are
+// exactly those of the warp passes in eik_forward.cuh; an iteration uses one
+// mode or the other for all its tiles (every CTA sees the same list size).
+#pragma once
+
+#include "eik_forward.cuh"
+
+namespace eik {
+
+template <int BX, int BY, int BZ>
+struct GroupGeom {
+    using G = TileGeom<BX, BY, BZ>;
+    static constexpr int CTA = 32 * kWarpsPerCta;
+    static constexpr int GT = G::V >= CTA ? CTA : G::V;   // threads per group
+    static constexpr int NG = CTA / GT;                    // groups per CTA
+    static constexpr int NPT = G::V / GT;                  // nodes per thread
+    static_assert(NG <= kWarpsPerCta && NG <= 8, "one staged block per group");
+};
+
+struct GroupCtl {
+    int tile;
+    unsigned key;
+    int nb[6];
+    float scale;
+    int fmask;
+    unsigned fmin[6];
+};
+
+__device__ __forceinline__ void group_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ int group_sync_or(int id, int n, int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.or.pred p, %2, %3, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(pred), "r"(id), "r"(n)
+        : "memory");
+    return r;
+}
+
+// Stage a tile for the group and relax it; returns the sweep count.
+template <class T, int BX, int BY, int BZ>
+__device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const GroupCtl &gc, int g, int gt, int bid,
+                                           T (&v)[GroupGeom<BX, BY, BZ>::NPT], unsigned &mine, bool &first_changed) {
+    using G = TileGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ>;
+    T tau[GG::NPT];
+    int c[GG::NPT];
+    const T *pg = P.phi_t + (size_t)g * G::V;
+    const T *tg = P.tau_t + (size_t)g * G::V;
+#pragma unroll
+    for (int m = 0; m < GG::NPT; ++m) {
+        const int q = gt + GG::GT * m;
+        v[m] = __ldcg(pg + q);
+        tau[m] = __ldcg(tg + q);
+        c[m] = G::sidx_of(q);
+        sm[c[m]] = v[m];
+    }
+    for (int h = gt; h < G::HALO_LOADED; h += GG::GT) {
+        int f, slot, src;
+        G::halo_of(h, f, slot, src);
+        const int n = gc.nb[f];
+        sm[slot] = n >= 0 ? __ldcg(P.phi_t + (size_t)n * G::V + src) : Num<T>::inf();
+    }
+    group_sync(bid, GG::GT);
+    mine = 0;
+    first_changed = false;
+    int s = 0;
+    for (;;) {
+        unsigned ch = 0;
+#pragma unroll
+        for (int m = 0; m < GG::NPT; ++m) {
+            if (!(tau[m] < T(0))) {
+                const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
+                const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
+                const T az = vmin(sm[c[m] - G::SX * G::SY], sm[c[m] + G::SX * G::SY]);
+                const T u = local_solve<T>(ax, ay, az, tau[m]);
+                if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
+            }
+        }
+        mine |= ch;
+        ++s;
+        const int any = group_sync_or(bid, GG::GT, ch != 0);
+        if (s == 1) first_changed = any != 0;
+        if (!any || s >= P.max_sweeps) break;
+    }
+#pragma unroll
+    for (int m = 0; m < GG::NPT; ++m)
+        if (mine >> m & 1) __stcg(P.phi_t + (size_t)g * G::V + gt + GG::GT * m, v[m]);
+    return s;
+}
+
+// Thread 0 of the group: tile id, key and neighbours of list entry idx.
+template <class T>
+__device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc, const int *in, int idx,
+                                            unsigned *kcur_or_null) {
+    const int g = __ldcg(in + idx);
+    gc.tile = g;
+    const int4 r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g));
+    const int4 r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4));
+    gc.key = kcur_or_null ? __ldcg(kcur_or_null + g) : kKeyInf;
+    if (kcur_or_null) __stcg(kcur_or_null + g, kKeyInf);   // no one writes this parity in this iteration
+    gc.nb[0] = r0.x; gc.nb[1] = r0.y; gc.nb[2] = r0.z; gc.nb[3] = r0.w; gc.nb[4] = r1.x; gc.nb[5] = r1.y;
+    gc.scale = __int_as_float(r1.w);
+    gc.fmask = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) gc.fmin[f] = kKeyInf;
+}
+
+// per-node face bits of node q
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>::faces_of(q); }
+
+// Step 2, latency mode.
+template <class T, int BX, int BY, int BZ>
+__device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, int it, int n, unsigned kmin_cur,
+                                  float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
+                                  long long &st_def) {
+    using G = TileGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ>;
+    Ctl *ctl = P.ctl;
+    const int nslot = (it + 1) % 3;
+    const int *in = (it & 1) ? P.list1 : P.list0;
+    int *out = (it & 1) ? P.list0 : P.list1;
+    unsigned *kcur = P.tkey + (size_t)(it & 1) * P.n_tiles;
+    unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
+    const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
+    T *sm = smbase + (size_t)gi * G::S;
+    GroupCtl &gc = gcs[gi];
+    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    n = min(n, P.n_tiles);
+    const int groups = gridDim.x * GG::NG;
+    for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
+        group_sync(bid, GG::GT);                       // previous visit fully done with gc
+        if (gt == 0) group_fetch(P, gc, in, idx, ord.on ? kcur : nullptr);
+        group_sync(bid, GG::GT);
+        const int g = gc.tile;
+        const unsigned key = gc.key;
+        if (ord.on && !order_visit(ord, key)) {       // deferred: listed again, not visited
+            if (gt < 32) {
+                if (gt == 0) { atomicMin(knext + g, key); st_def++; }
+                warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, gt == 0, g, &ctl->kmin[nslot], key);
+            }
+            continue;
+        }
+        T v[GG::NPT];
+        unsigned mine;
+        bool changed;
+        const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
+        if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
+        if (changed && (!P.one_visit || s >= P.max_sweeps)) {
+            if (gt < 32) {
+                if (ord.on && gt == 0) atomicMin(knext + g, key);
+                warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, gt == 0, g, ord.on ? &ctl->kmin[nslot] : nullptr, key);
+            }
+            continue;
+        }
+        // converged: Active -> Source, Distant face neighbours become Active
+        if (ord.on) {
+#pragma unroll
+            for (int m = 0; m < GG::NPT; ++m) {
+                const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                for (int f = 0; f < 6; ++f)
+                    if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+            }
+            group_sync(bid, GG::GT);
+        }
+        if (gt < 32) {
+            if (gt == 0) __stcg(P.tstate + g, (int)kSource);
+            const int nbf = gt < 6 ? gc.nb[gt] : -1;
+            const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
+            const bool act = prev == (int)kDistant;
+            unsigned kf = kKeyInf;
+            if (ord.on && nbf >= 0) {
+                kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+            }
+            warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, act, nbf, ord.on ? &ctl->kmin[nslot] : nullptr, kf);
+        }
+    }
+}
+
+// Step 3b, latency mode.
+template <class T, int BX, int BY, int BZ>
+__device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, int r, int n, unsigned kmin_cur,
+                                  float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
+                                  long long &st_def) {
+    using G = TileGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ>;
+    Ctl *ctl = P.ctl;
+    const int nslot = (r + 1) % 3;
+    const int *in = (r & 1) ? P.list1 : P.list0;
+    int *out = (r & 1) ? P.list0 : P.list1;
+    unsigned *kcur = P.tkey + (size_t)(r & 1) * P.n_tiles;
+    unsigned *knext = P.tkey + (size_t)((r + 1) & 1) * P.n_tiles;
+    const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
+    T *sm = smbase + (size_t)gi * G::S;
+    GroupCtl &gc = gcs[gi];
+    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    n = min(n, P.n_tiles);
+    const int next_stamp = r + 2;
+    const int groups = gridDim.x * GG::NG;
+    for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
+        group_sync(bid, GG::GT);
+        if (gt == 0) group_fetch(P, gc, in, idx, ord.on ? kcur : nullptr);
+        group_sync(bid, GG::GT);
+        const int g = gc.tile;
+        const unsigned key = gc.key;
+        if (ord.on && !order_visit(ord, key)) {
+            if (gt < 32) {
+                bool want = false;
+                if (gt == 0) {
+                    atomicMin(knext + g, key);
+                    want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
+                    st_def++;
+                }
+                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, &ctl->rkmin[nslot], key);
+            }
+            continue;
+        }
+        T v[GG::NPT];
+        unsigned mine;
+        bool changed;
+        const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
+        if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
+        // faces where a node dropped, and (ordered) the smallest dropped value on each
+#pragma unroll
+        for (int m = 0; m < GG::NPT; ++m) {
+            if (!(mine >> m & 1)) continue;
+            const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+            if (fb) {
+                atomicOr(&gc.fmask, fb);
+                if (ord.on)
+                    for (int f = 0; f < 6; ++f)
+                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+            }
+        }
+        group_sync(bid, GG::GT);
+        if (gt < 32) {
+            const int fm = gc.fmask;
+            int cand = -1;
+            if (gt < 6 && (fm >> gt & 1)) cand = gc.nb[gt];
+            if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+            unsigned kc = kKeyInf;
+            if (ord.on && cand >= 0) {
+                kc = gt == 6 ? key : scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                atomicMin(knext + cand, kc);
+            }
+            const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+            if (ord.on && cand >= 0 && !want) atomicMin(&ctl->rkmin[nslot], kc);
+            warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
+        }
+    }
+}
+
+}  // namespace eik

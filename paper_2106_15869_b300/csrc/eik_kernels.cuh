@@ -1,0 +1,396 @@
+// eik_kernels.cuh -- the kernels of the forward solve: descriptor upload,
+// Step 1 (k_init, k_sources), the Step-2/3 loops (one cooperative persistent
+// launch, or one launch per iteration), and the output unpack.  Each
+// iteration of a loop runs in latency mode (a thread group per tile,
+// eik_group.cuh) when its list is short and in throughput mode (a warp per
+// tile, eik_forward.cuh) otherwise.
+#pragma once
+
+#include <cstddef>
+
+#include "eik_forward.cuh"
+#include "eik_group.cuh"
+
+namespace eik {
+
+// latency mode when the list holds at most this many tiles per thread group
+constexpr int kGroupModeFactor = 2;
+
+// ---------------------------------------------------------------- kernels
+// Descriptor upload (by-value parameter, so that the call can be captured).
+__global__ void k_write_desc(InstDesc *desc, double *inst_acc, DescChunk chunk) {
+    const int i = threadIdx.x;
+    if (i < chunk.count) {
+        desc[chunk.first + i] = chunk.d[i];
+        double *a = inst_acc + 4 * (chunk.first + i);
+        a[0] = 0.0;                                   // sum of F over passable nodes
+        a[1] = 0.0;                                   // their count
+        reinterpret_cast<unsigned *>(a + 2)[0] = 0x7f800000u;   // min F (as float bits)
+        reinterpret_cast<unsigned *>(a + 3)[0] = 0u;            // max F (as float bits)
+    }
+}
+
+// 1/delta per instance for the ordered schedule: delta = order * (mean tile
+// edge) * h / mean(F over passable nodes).
+// An instance whose passable speeds span more than kOrderContrast (e.g. slow
+// walls in a fast medium) spreads its keys over too many buckets; it is left
+// unordered (scale 0).
+constexpr double kOrderContrast = 100.0;
+
+template <int BX, int BY, int BZ>
+__global__ void k_scale(const InstDesc *desc, const double *inst_acc, float *inst_scale, int B, float order) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
+    const double *a = inst_acc + 4 * b;
+    const double cnt = a[1], sum = a[0];
+    const double fmn = __uint_as_float(reinterpret_cast<const unsigned *>(a + 2)[0]);
+    const double fmx = __uint_as_float(reinterpret_cast<const unsigned *>(a + 3)[0]);
+    const double meanF = cnt > 0 ? sum / cnt : 0.0;
+    double sc = meanF > 0 ? meanF / ((double)order * edge * desc[b].h) : 1.0;
+    if (!(sc > 0) || !(sc < 1e30)) sc = 1.0;
+    if (cnt > 0 && fmx > kOrderContrast * fmn) sc = 0.0;
+    inst_scale[b] = (float)sc;
+}
+
+// Step 1a: bricked tau = h/F and phi = +inf; per-tile state and neighbour
+// ids; control block.  One CTA of V threads per tile.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX *BY *BZ) k_init(FwdParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    __shared__ int s_b;
+    const int g = blockIdx.x;
+    if (threadIdx.x == 0) s_b = find_inst_by_tile(P.desc, P.B, g);
+    __syncthreads();
+    const InstDesc &d = P.desc[s_b];
+    const long long l = g - d.tile_base;
+    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    const int tid = threadIdx.x;
+    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
+    T tau = Num<T>::inf();
+    double fsum = 0.0, fcnt = 0.0;
+    if (i < d.nx && j < d.ny && k < d.nz) {
+        const T f = P.F[d.in_off + ((long long)k * d.ny + j) * d.nx + i];
+        if (f > T(0)) { tau = T(d.h) / f; fsum = (double)f; fcnt = 1.0; }
+    }
+    P.tau_t[(size_t)g * G::V + tid] = tau;
+    P.phi_t[(size_t)g * G::V + tid] = Num<T>::inf();
+    if (tid == 0) {
+        P.tile_inst[g] = s_b;
+        P.tstate[g] = kDistant;
+        P.tstamp[g] = 0;
+        P.tkey[g] = kKeyInf;
+        P.tkey[P.n_tiles + g] = kKeyInf;
+    }
+    if (P.ordered) {   // per-instance mean, min and max speed for the bucket width
+        float fmn = fcnt > 0 ? (float)fsum : __int_as_float(0x7f800000), fmx = fcnt > 0 ? (float)fsum : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+            fcnt += __shfl_xor_sync(0xffffffffu, fcnt, o);
+            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+        }
+        if ((tid & 31) == 0 && fcnt > 0) {
+            atomicAdd(P.inst_acc + 4 * s_b, fsum);
+            atomicAdd(P.inst_acc + 4 * s_b + 1, fcnt);
+            // positive floats order like their bit patterns
+            atomicMin(reinterpret_cast<unsigned *>(P.inst_acc + 4 * s_b + 2), __float_as_uint(fmn));
+            atomicMax(reinterpret_cast<unsigned *>(P.inst_acc + 4 * s_b + 3), __float_as_uint(fmx));
+        }
+    }
+    if (tid < 8) {
+        int nb;
+        switch (tid) {
+            case 0: nb = tx > 0 ? g - 1 : -1; break;
+            case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
+            case 2: nb = ty > 0 ? g - d.tx : -1; break;
+            case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
+            case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
+            case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
+            case 6: nb = s_b; break;
+            default: nb = __float_as_int(1.0f); break;   // key scale, set by k_tile_scale
+        }
+        P.tile_nb[8 * g + tid] = nb;
+    }
+    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
+        const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
+        reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+    }
+}
+
+// the instance key scale into every tile record (ordered schedule)
+__global__ void k_tile_scale(int *tile_nb, const float *inst_scale, int n_tiles) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_tiles; g += gridDim.x * blockDim.x)
+        tile_nb[8 * g + 7] = __float_as_int(inst_scale[tile_nb[8 * g + 6]]);
+}
+
+__device__ __forceinline__ void atomic_min_val(float *p, float v) {
+    int old = __float_as_int(*(volatile float *)p);
+    while (v < __int_as_float(old)) {
+        const int prev = atomicCAS(reinterpret_cast<int *>(p), old, __float_as_int(v));
+        if (prev == old) break;
+        old = prev;
+    }
+}
+__device__ __forceinline__ void atomic_min_val(double *p, double v) {
+    unsigned long long old = __double_as_longlong(*(volatile double *)p);
+    while (v < __longlong_as_double(old)) {
+        const unsigned long long prev =
+            atomicCAS(reinterpret_cast<unsigned long long *>(p), old, (unsigned long long)__double_as_longlong(v));
+        if (prev == old) break;
+        old = prev;
+    }
+}
+
+// Step 1b: sources fixed (phi = value, tau = -1 marker); Active = the tiles
+// that hold the sources' face neighbours (the source tile and, for a source on
+// a tile face, the tile across that face).
+template <class T, int BX, int BY, int BZ>
+__global__ void k_sources(FwdParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P.n_src) return;
+    const int b = find_inst_by_src(P.desc, P.B, s);
+    const InstDesc &d = P.desc[b];
+    if (s < d.src_begin || s >= d.src_end) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
+    const long long p = P.src_idx[s];
+    const long long N = (long long)d.nx * d.ny * d.nz;
+    if (p < 0 || p >= N) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
+    const int i = (int)(p % d.nx), j = (int)((p / d.nx) % d.ny), k = (int)(p / ((long long)d.nx * d.ny));
+    const int tx = i / BX, ty = j / BY, tz = k / BZ;
+    const int g = (int)(d.tile_base + ((long long)tz * d.ty + ty) * d.tx + tx);
+    const int loc = ((k % BZ) * BY + (j % BY)) * BX + (i % BX);
+    atomic_min_val(P.phi_t + (size_t)g * G::V + loc, P.src_val[s]);
+    P.tau_t[(size_t)g * G::V + loc] = T(-1);
+    int cand[7];
+    int nc = 0;
+    cand[nc++] = g;
+    if (i % BX == 0 && i > 0) cand[nc++] = g - 1;
+    if (i % BX == BX - 1 && i + 1 < d.nx) cand[nc++] = g + 1;
+    if (j % BY == 0 && j > 0) cand[nc++] = g - d.tx;
+    if (j % BY == BY - 1 && j + 1 < d.ny) cand[nc++] = g + d.tx;
+    if (k % BZ == 0 && k > 0) cand[nc++] = g - d.tx * d.ty;
+    if (k % BZ == BZ - 1 && k + 1 < d.nz) cand[nc++] = g + d.tx * d.ty;
+    const unsigned key = scaled_key((float)P.src_val[s], P.inst_scale[b]);
+    for (int q = 0; q < nc; ++q) {
+        if (P.ordered) {
+            atomicMin(P.tkey + cand[q], key);
+            atomicMin(&P.ctl->kmin[0], key);
+        }
+        if (atomicCAS(P.tstate + cand[q], (int)kDistant, (int)kActive) == (int)kDistant) {
+            const int pos = atomicAdd(&P.ctl->cnt[0], 1);
+            if (pos < P.n_tiles) P.list0[pos] = cand[q];
+            else atomicOr(&P.ctl->flags, kFlagOverflow);
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void flush_stats(const FwdParams<T> &P, long long a, long long b, long long c,
+                                            long long d, long long e) {
+    if (lane_id() == 0) {
+        if (e) atomicAdd((unsigned long long *)&P.ctl->tiles_deferred, (unsigned long long)e);
+        if (a) atomicAdd((unsigned long long *)&P.ctl->tiles_update, (unsigned long long)a);
+        if (b) atomicAdd((unsigned long long *)&P.ctl->tiles_flagged, (unsigned long long)b);
+        if (c) atomicAdd((unsigned long long *)&P.ctl->tiles_remedy, (unsigned long long)c);
+        if (d) atomicAdd((unsigned long long *)&P.ctl->sweeps, (unsigned long long)d);
+    }
+}
+
+// resident CTAs per SM asked of the compiler (register budget per thread =
+// 65536 / (32 * kWarpsPerCta * this)): more warps in flight for small tiles
+template <class T, int BX, int BY, int BZ>
+constexpr int min_ctas() {
+    return sizeof(T) == 8 ? 2   // FP64 validation mode: registers over occupancy
+           : TileGeom<BX, BY, BZ>::NPL <= 2 ? 6 : TileGeom<BX, BY, BZ>::NPL <= 4 ? 5
+           : TileGeom<BX, BY, BZ>::NPL <= 8 ? 3 : 2;
+}
+
+template <class T, int BX, int BY, int BZ>
+struct WarpSmem {
+    T phi[kWarpsPerCta][TileGeom<BX, BY, BZ>::S];
+};
+
+// Steps 2 and 3 in one cooperative launch; iterations are separated by the
+// bounded grid barrier.  Every warp reads the same list size after a
+// barrier, so all CTAs leave the loops together.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_persistent(FwdParams<T> P) {
+    __shared__ WarpSmem<T, BX, BY, BZ> sm;
+    __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ int s_n, s_p, s_visits;
+    __shared__ unsigned s_k;
+    T *my = sm.phi[warp_in_cta()];
+    init_stage<T, BX, BY, BZ>(my);
+    if (threadIdx.x == 0) s_visits = 0;
+    const int groups = gridDim.x * GroupGeom<BX, BY, BZ>::NG;
+    float width = 1.0f;
+    int n_prev = 0;
+    Ctl *ctl = P.ctl;
+    unsigned long long target = 0;
+    long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0, deferred = 0;
+    int it = 0, r = 0;
+    for (;; ++it) {
+        if (threadIdx.x == 0) {
+            s_n = ld_volatile(&ctl->cnt[it % 3]);
+            s_k = ld_volatile_u(&ctl->kmin[it % 3]);
+            s_p = it > 0 ? ld_volatile(&ctl->nproc[(it - 1) % 4]) : 0;
+        }
+        __syncthreads();
+        const int n = s_n;
+        const unsigned kq = s_k;
+        if (it > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
+        n_prev = n;
+        if (n == 0) break;
+        if (it >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {   // slot (it+2)%3 was last read in iteration it-1
+            ctl->cnt[(it + 2) % 3] = 0;
+            ctl->kmin[(it + 2) % 3] = kKeyInf;
+            ctl->nproc[(it + 2) % 4] = 0;
+        }
+        if (n <= kGroupModeFactor * groups)
+            update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
+        else
+            update_pass<T, BX, BY, BZ>(P, my, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[it % 4], s_visits); s_visits = 0; }
+        if (!grid_sync(ctl, target)) goto done;
+    }
+    if (P.skip_remedy) goto done;
+    detect_pass<T, BX, BY, BZ>(P, my, t_flag);
+    if (!grid_sync(ctl, target)) goto done;
+    // the Step-2 counters are idle from here on: nproc slots restart for Step 3
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) ctl->nproc[q] = 0;
+    if (!grid_sync(ctl, target)) goto done;
+    width = 1.0f;
+    n_prev = 0;
+    for (;; ++r) {
+        if (threadIdx.x == 0) {
+            s_n = ld_volatile(&ctl->rcnt[r % 3]);
+            s_k = ld_volatile_u(&ctl->rkmin[r % 3]);
+            s_p = r > 0 ? ld_volatile(&ctl->nproc[(r - 1) % 4]) : 0;
+        }
+        __syncthreads();
+        const int n = s_n;
+        const unsigned kq = s_k;
+        if (r > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
+        n_prev = n;
+        if (n == 0) break;
+        if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->rcnt[(r + 2) % 3] = 0;
+            ctl->rkmin[(r + 2) % 3] = kKeyInf;
+            ctl->nproc[(r + 2) % 4] = 0;
+        }
+        if (n <= kGroupModeFactor * groups)
+            remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
+        else
+            remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
+        if (!grid_sync(ctl, target)) goto done;
+    }
+done:
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->iters_update = it;
+        ctl->iters_remedy = r;
+    }
+    flush_stats<T>(P, t_upd, t_flag, t_rem, sweeps, deferred);
+}
+
+// Host-loop schedule: one launch per iteration.  The bucket width of
+// iteration it comes from the width of it-1 (ctl->win by parity: launch it
+// reads slot (it-1)&1 and its block 0 writes slot it&1) and the visits of it-1.
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ float host_loop_width(Ctl *ctl, int it, int n, int prev_n) {
+    (void)n;
+    const float w_prev = it > 0 ? *(volatile float *)&ctl->win[(it - 1) & 1] : 1.0f;
+    const float w = it > 0 ? adapt_window(w_prev, ld_volatile(&ctl->nproc[(it - 1) % 4]), prev_n,
+                                          (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG, (int)gridDim.x * kWarpsPerCta)
+                           : 1.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->win[it & 1] = w;
+    return w;
+}
+
+// Host-loop schedule: one launch per iteration.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_update_iter(FwdParams<T> P, int it,
+                                                                                              int prev_n) {
+    __shared__ WarpSmem<T, BX, BY, BZ> sm;
+    __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ int s_visits;
+    const int n = ld_volatile(&P.ctl->cnt[it % 3]);
+    const unsigned kq = ld_volatile_u(&P.ctl->kmin[it % 3]);
+    const float width = host_loop_width<BX, BY, BZ>(P.ctl, it, n, prev_n);
+    long long t = 0, s = 0, d = 0;
+    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
+    if (threadIdx.x == 0) s_visits = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.ctl->cnt[(it + 2) % 3] = 0;
+        P.ctl->kmin[(it + 2) % 3] = kKeyInf;
+        P.ctl->nproc[(it + 2) % 4] = 0;
+    }
+    __syncthreads();
+    if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
+        update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t, s, d);
+    else
+        update_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], it, n, kq, width, &s_visits, t, s, d);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_visits) atomicAdd(&P.ctl->nproc[it % 4], s_visits);
+    flush_stats<T>(P, t, 0, 0, s, d);
+}
+
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_detect(FwdParams<T> P) {
+    __shared__ WarpSmem<T, BX, BY, BZ> sm;
+    long long f = 0;
+    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
+    detect_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], f);
+    flush_stats<T>(P, 0, f, 0, 0, 0);
+}
+
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_remedy_iter(FwdParams<T> P, int r,
+                                                                                              int prev_n) {
+    __shared__ WarpSmem<T, BX, BY, BZ> sm;
+    __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ int s_visits;
+    const int n = ld_volatile(&P.ctl->rcnt[r % 3]);
+    const unsigned kq = ld_volatile_u(&P.ctl->rkmin[r % 3]);
+    const float width = host_loop_width<BX, BY, BZ>(P.ctl, r, n, prev_n);
+    long long t = 0, s = 0, d = 0;
+    init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
+    if (threadIdx.x == 0) s_visits = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.ctl->rcnt[(r + 2) % 3] = 0;
+        P.ctl->rkmin[(r + 2) % 3] = kKeyInf;
+        P.ctl->nproc[(r + 2) % 4] = 0;
+    }
+    __syncthreads();
+    if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
+        remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t, s, d);
+    else
+        remedy_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], r, n, kq, width, &s_visits, t, s, d);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_visits) atomicAdd(&P.ctl->nproc[r % 4], s_visits);
+    flush_stats<T>(P, 0, 0, t, s, d);
+}
+
+// Output: bricked phi -> caller's row-major phi.  One CTA of V threads per tile.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX *BY *BZ) k_unpack(FwdParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    const int g = blockIdx.x;
+    const int b = P.tile_inst[g];
+    const InstDesc &d = P.desc[b];
+    const long long l = g - d.tile_base;
+    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    const int tid = threadIdx.x;
+    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
+    if (i < d.nx && j < d.ny && k < d.nz)
+        P.phi_out[d.out_off + ((long long)k * d.ny + j) * d.nx + i] = P.phi_t[(size_t)g * G::V + tid];
+}
+
+}  // namespace eik

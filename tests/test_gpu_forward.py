@@ -77,7 +77,7 @@ def test_maze_small(dtype):
     assert_parity(got, oracle_phi(inst, dtype), TOL32 if dtype == "fp32" else TOL64)
 
 
-@pytest.mark.parametrize("schedule", ["persistent", "hostloop"])
+@pytest.mark.parametrize("schedule", ["persistent", "hostloop", "async"])
 def test_schedules_agree(schedule):
     inst = W.maze_3d(48, seed=7, n_slabs=3, gap=10, n_src=3)
     got, st = gpu_solve(inst, "fp64", schedule=schedule)
@@ -239,3 +239,60 @@ def test_full_oscillating_256_fp32():
     got, st = gpu_solve(inst, "fp32")
     err = assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
     print("oscillating_3d_256 max rel err", err, st)
+
+
+# ------------------------------------------------------------------ asynchronous schedule
+@pytest.mark.parametrize("seed", range(12))
+def test_async_random_small_grids(seed):
+    inst = W.random_small(100 + seed, max_edge=25, p_barrier=0.08 if seed % 2 else 0.0)
+    got, st = gpu_solve(inst, "fp64", schedule="async")
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+
+
+@pytest.mark.parametrize("tile", ["4x4x4", "8x4x4", "8x8x4", "8x8x8"])
+def test_async_oscillating_and_maze(tile):
+    inst = W.oscillating_3d(50)
+    got, st = gpu_solve(inst, "fp32", schedule="async", tile=tile)
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+    inst = W.maze_3d(56, seed=9, n_slabs=4, gap=9, n_src=3)
+    got, st = gpu_solve(inst, "fp32", schedule="async", tile=tile)
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
+def test_async_batched_and_2d():
+    from paper_2106_15869_b300 import api
+    torch = _torch()
+    insts = W.lognormal_batch(B=4, seed=8, lo=24, hi=40)
+    probs = [(torch.as_tensor(i.F, dtype=torch.float32).cuda(), i.src_idx, i.h) for i in insts]
+    outs = api.solve_batched(probs, schedule="async")
+    for i, o in zip(insts, outs):
+        assert_parity(o.cpu().double().numpy(), oracle_phi(i, "fp32"), TOL32)
+    inst = W.paper_example_2d(5, n=180)
+    got, _ = gpu_solve(inst, "fp32", schedule="async")
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
+def test_async_skip_remedy_and_cap():
+    torch = _torch()
+    from paper_2106_15869_b300 import api, EikonalError
+    inst = W.maze_3d(48, seed=3, n_slabs=4, gap=8, n_src=3)
+    ref = oracle_phi(inst, "fp64")
+    upd, st = gpu_solve(inst, "fp64", schedule="async", skip_remedy=True)
+    fin = np.isfinite(ref)
+    assert np.all(upd[fin] >= ref[fin] - 1e-12)
+    F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
+    with pytest.raises(EikonalError) as e:
+        api.solve(F, inst.src_idx, inst.h, schedule="async", max_iters=1, return_stats=True)
+    assert e.value.code == 2
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "async"])
+@pytest.mark.parametrize("order", [-1.0, 4.0])
+def test_converge_sweep_rule(schedule, order):
+    """Step-2 convergence taken at sweep granularity reaches the same solution."""
+    inst = W.maze_3d(60, seed=5, n_slabs=4, gap=9, n_src=3)
+    got, st = gpu_solve(inst, "fp64", schedule=schedule, order=order, converge="sweep")
+    assert_parity(got, oracle_phi(inst, "fp64"), TOL64)
+    inst = W.oscillating_3d(44)
+    got, st = gpu_solve(inst, "fp32", schedule=schedule, order=order, converge="sweep", tile="8x4x4")
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
