@@ -158,6 +158,24 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
                       void *phi_packed, const int64_t *phi_offsets, void *workspace,
                       size_t workspace_bytes, void *stream, const eik_options *opt, eik_stats *stats);
 
+/*
+ * eik_solve without any device allocation and without a workspace argument.
+ * The paper has no counterpart: this is for callers that must not allocate
+ * device memory at solve time -- e.g. a latency-critical loop that cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree imply, or a host
+ * framework that owns all device memory and cannot lend a workspace.
+ * Scratch comes from one static device array of 64 MiB built into the
+ * library (held by every GPU that loads it, until the process exits); grids
+ * whose eik_workspace_size() exceeds it are rejected with EIK_ERR_ARG.  The
+ * first call on a device resolves the array's device address (a one-time
+ * set-up per device): make that first call before any stream capture.  All
+ * calls share the one array: calls whose work overlaps on a GPU race and
+ * corrupt each other's results, so serialise them (one stream, or events).
+ * Arguments, results and errors as for eik_solve.
+ */
+int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_idx, const void *src_val,
+                      int64_t n_src, void *phi, void *stream, const eik_options *opt, eik_stats *stats);
+
 /* thread-local message describing the last non-zero return (never NULL) */
 const char *eik_last_error(void);
 

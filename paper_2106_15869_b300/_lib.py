@@ -95,6 +95,9 @@ def _optional_symbols(lib):
     G = ctypes.POINTER(eik_grid)
     O = ctypes.POINTER(eik_options)
     S = ctypes.POINTER(eik_stats)
+    if hasattr(lib, "eik_solve_noalloc"):
+        lib.eik_solve_noalloc.restype = ctypes.c_int
+        lib.eik_solve_noalloc.argtypes = [G, _vp, _vp, _vp, _i64, _vp, _vp, O, S]
     if hasattr(lib, "eik_adjoint_workspace_size_batched"):
         lib.eik_adjoint_workspace_size_batched.restype = _sz
         lib.eik_adjoint_workspace_size_batched.argtypes = [_i64, G, O]

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -454,6 +455,33 @@ int solve_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F
     return dispatch_tile<float>(L, o, w, F, src_idx, src_val, n_src, phi, st, stats);
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+// Fixed scratch for eik_solve_noalloc: a file-scope device array, so a caller
+// that may not allocate device memory still gets a workspace.  Every device
+// that loads this library holds these bytes until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, resolved once
+// per device (the host-side name of the array is not a device address).
+int noalloc_scratch(void **out) {
+    int dev = -1;
+    EIK_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(EIK_ERR_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        EIK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return EIK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -488,6 +516,26 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
     if (!F_offsets || !src_offsets || !phi_offsets) return fail(EIK_ERR_ARG, "offset arrays must be non-NULL");
     return solve_impl(B, grids, F_packed, F_offsets, src_idx, src_val, src_offsets, phi_packed, phi_offsets,
                       workspace, workspace_bytes, stream, opt, stats);
+}
+
+int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_idx, const void *src_val,
+                      int64_t n_src, void *phi, void *stream, const eik_options *opt, eik_stats *stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n_src < 0) return fail(EIK_ERR_ARG, "n_src must be >= 0");
+    const size_t need = eik_workspace_size(grid, opt);
+    if (need == 0) return fail(EIK_ERR_ARG, "invalid grid or options");
+    if (need > kNoAllocScratchBytes)
+        return fail(EIK_ERR_ARG,
+                    "grid needs %zu bytes of scratch but the static scratch of eik_solve_noalloc holds %zu; "
+                    "call eik_solve with a caller-provided workspace instead",
+                    need, kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // the solve initialises every part of the workspace it reads (control
+    // block, per-tile state, keys, lists), so stale contents of the shared
+    // array from an earlier call do not matter
+    return eik_solve(grid, F, src_idx, src_val, n_src, phi, scratch, kNoAllocScratchBytes, stream, opt, stats);
 }
 
 const char *eik_last_error(void) { return g_err.c_str(); }
