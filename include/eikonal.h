@@ -159,6 +159,34 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
                       size_t workspace_bytes, void *stream, const eik_options *opt, eik_stats *stats);
 
 /*
+ * Adjoint of the discrete solve (not in the paper): the gradient dL/ds of a
+ * loss L(phi) with respect to slowness s = 1/F, by the adjoint-state method
+ * applied to the eq.-(6) residual G_i = sum_d ((phi_i - m_{i,d})^+)^2 - h^2 s_i^2
+ * (m_{i,d}: the selected upwind neighbour on axis d, argmin of the two, the
+ * lower flat index on a tie).  lambda solves J^T lambda = r with r = dL/dphi;
+ * dL/ds_i = 2 h^2 s_i lambda_i, and 0 at sources, unreachable and impassable
+ * nodes.  phi is the forward solution (a checkpoint, typically from
+ * eik_solve_batched with the same grids, F and sources).
+ *   grids, F_packed, F_offsets, src_idx, src_offsets   as for eik_solve_batched
+ *   phi_packed/phi_offsets   device forward solutions, one [nz][ny][nx] block per instance
+ *   r_packed                 device dL/dphi, same offsets as phi
+ *   g_packed/g_offsets       device output, ACCUMULATED (g += dL/ds); instances may share a
+ *                            block (g_offsets equal) to sum their gradients
+ * stats (nullable): tiles_remedy = adjoint tile visits, iters_remedy = iterations.
+ * Workspace: eik_adjoint_workspace_size_batched (4 arrays of the precision per node).
+ */
+size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt);
+int eik_adjoint_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,
+                        const void *phi_packed, const int64_t *phi_offsets, const int64_t *src_idx,
+                        const int64_t *src_offsets, const void *r_packed, void *g_packed, const int64_t *g_offsets,
+                        void *workspace, size_t workspace_bytes, void *stream, const eik_options *opt,
+                        eik_stats *stats);
+/* one grid: F, phi, r, g device [nz][ny][nx]; src_idx device [n_src]; g accumulated */
+int eik_adjoint(const eik_grid *grid, const void *F, const void *phi, const int64_t *src_idx, int64_t n_src,
+                const void *r, void *g, void *workspace, size_t workspace_bytes, void *stream,
+                const eik_options *opt, eik_stats *stats);
+
+/*
  * eik_solve without any device allocation and without a workspace argument.
  * The paper has no counterpart: this is for callers that must not allocate
  * device memory at solve time -- e.g. a latency-critical loop that cannot

@@ -6,15 +6,15 @@ remedy pass), in hand-written CUDA kernels behind the C ABI of
 ``libeikonal.so`` (include/eikonal.h).
 
 Public API (loaded lazily, so that ``workloads`` imports without CUDA):
-  solve, solve_batched, Workspace, EikonalError
+  solve, solve_batched, adjoint, adjoint_batched, EikonalFn, Workspace, EikonalError
 """
 from __future__ import annotations
 
-__all__ = ["solve", "solve_batched", "Workspace", "EikonalError"]
+__all__ = ["solve", "solve_batched", "adjoint", "adjoint_batched", "EikonalFn", "Workspace", "EikonalError"]
 
 
 def __getattr__(name):
-    if name in ("solve", "solve_batched", "Workspace"):
+    if name in ("solve", "solve_batched", "adjoint", "adjoint_batched", "EikonalFn", "Workspace"):
         from . import api
         return getattr(api, name)
     if name == "EikonalError":

@@ -103,8 +103,11 @@ def _optional_symbols(lib):
         lib.eik_adjoint_workspace_size_batched.argtypes = [_i64, G, O]
     if hasattr(lib, "eik_adjoint_batched"):
         lib.eik_adjoint_batched.restype = ctypes.c_int
-        lib.eik_adjoint_batched.argtypes = [_i64, G, _vp, _pi64, _vp, _pi64, _vp, _vp, _pi64, _vp,
-                                            _pi64, _vp, _sz, _vp, O, S]
+        lib.eik_adjoint_batched.argtypes = [_i64, G, _vp, _pi64, _vp, _pi64, _vp, _pi64, _vp, _vp, _pi64,
+                                            _vp, _sz, _vp, O, S]
+    if hasattr(lib, "eik_adjoint"):
+        lib.eik_adjoint.restype = ctypes.c_int
+        lib.eik_adjoint.argtypes = [G, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp, O, S]
 
 
 def check(rc: int):

@@ -178,3 +178,110 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
     for q, F in enumerate(Fs):
         outs.append(phi_packed[phi_off[q]:phi_off[q] + sizes[q]].view(F.shape))
     return (outs, st.as_dict()) if return_stats else outs
+
+
+def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances: bool = False, tile="auto",
+                    max_iters=0, return_stats=False, workspace: Workspace | None = None):
+    """Gradients dL/ds (s = 1/F) of a loss L(phi) by the adjoint of the discrete solve.
+
+    problems: list of (F, src_idx, h) as for solve_batched (all on one CUDA
+    device, one dtype); phis: the forward solutions (checkpoints); rs: dL/dphi
+    per instance (same shapes).  With shared_F every instance uses the first
+    F; with sum_instances the gradients of all instances are accumulated into
+    one tensor shaped like the first F (e.g. many shots on one slowness model).
+    Returns a list of gradients, or one tensor with sum_instances.
+    """
+    if not problems:
+        raise ValueError("no problems")
+    F0 = problems[0][0]
+    dev, dtype = F0.device, F0.dtype
+    if dtype not in _DT or not F0.is_cuda:
+        raise TypeError("F must be a float32/float64 CUDA tensor")
+    if len(phis) != len(problems) or len(rs) != len(problems):
+        raise ValueError("one phi and one r per problem")
+    dims, Fs, idxs = [], [], []
+    for pr in problems:
+        F = F0 if shared_F else pr[0]
+        if F.device != dev or F.dtype != dtype:
+            raise ValueError("all F must share device and dtype")
+        nx, ny, nz = _dims(F)
+        dims.append((nx, ny, nz, pr[2]))
+        Fs.append(F)
+        idxs.append(_as_index(pr[1], dev))
+    if sum_instances and any(d[:3] != dims[0][:3] for d in dims):
+        raise ValueError("sum_instances needs equal grid shapes")
+    sizes = [d[0] * d[1] * d[2] for d in dims]
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    for q, (ph, r) in enumerate(zip(phis, rs)):
+        if ph.numel() != sizes[q] or r.numel() != sizes[q]:
+            raise ValueError("phi and r must match their grid")
+    if shared_F:
+        F_packed, F_off = F0.contiguous().reshape(-1), np.zeros(len(problems), dtype=np.int64)
+    else:
+        F_packed, F_off = torch.cat([F.contiguous().reshape(-1) for F in Fs]), off
+    phi_packed = torch.cat([ph.to(dev, dtype).contiguous().reshape(-1) for ph in phis])
+    r_packed = torch.cat([r.to(dev, dtype).contiguous().reshape(-1) for r in rs])
+    if sum_instances:
+        g_packed = torch.zeros(sizes[0], dtype=dtype, device=dev)
+        g_off = np.zeros(len(problems), dtype=np.int64)
+    else:
+        g_packed = torch.zeros(int(sum(sizes)), dtype=dtype, device=dev)
+        g_off = off
+    nsrc = [i.numel() for i in idxs]
+    src_off = np.concatenate([[0], np.cumsum(nsrc)]).astype(np.int64)
+    src_idx = torch.cat(idxs) if sum(nsrc) else torch.zeros(0, dtype=torch.int64, device=dev)
+    lib = _lib.load()
+    g = _lib.grids_array(dims)
+    opt = _lib.make_options(tile, "auto", _DT[dtype], False, max_iters)
+    B = len(problems)
+    nbytes = lib.eik_adjoint_workspace_size_batched(B, g, ctypes.byref(opt))
+    if nbytes == 0:
+        raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grids or options")
+    with torch.cuda.device(dev):
+        buf = _workspace(dev, nbytes, workspace)
+        st = _lib.eik_stats()
+        rc = lib.eik_adjoint_batched(B, g, F_packed.data_ptr(), _lib.i64_array(F_off), phi_packed.data_ptr(),
+                                     _lib.i64_array(off), src_idx.data_ptr() if src_idx.numel() else None,
+                                     _lib.i64_array(src_off), r_packed.data_ptr(), g_packed.data_ptr(),
+                                     _lib.i64_array(g_off), buf.data_ptr(), buf.numel(), _stream_ptr(),
+                                     ctypes.byref(opt), ctypes.byref(st) if return_stats else None)
+        _lib.check(rc)
+    if sum_instances:
+        out = g_packed.view(F0.shape)
+    else:
+        out = [g_packed[off[q]:off[q] + sizes[q]].view(Fs[q].shape) for q in range(B)]
+    return (out, st.as_dict()) if return_stats else out
+
+
+def adjoint(F, src_idx, h, phi, r, **kw):
+    """dL/ds for one grid (see adjoint_batched)."""
+    return adjoint_batched([(F, src_idx, h)], [phi], [r], **kw)[0]
+
+
+class EikonalFn(torch.autograd.Function):
+    """phi = EikonalFn.apply(s, sources, h): arrival times for slowness s = 1/F.
+
+    s: (ny, nx) or (nz, ny, nx) CUDA tensor (float32, or float64 for the
+    validation mode); sources: list of source-index arrays, one per shot;
+    h: spacing.  Returns phi stacked over shots, shape (n_shots, *s.shape).
+    The forward runs all shots as one batched solve on a shared speed map and
+    checkpoints phi; backward runs the batched adjoint and sums the shots'
+    gradients into dL/ds.
+    """
+
+    @staticmethod
+    def forward(ctx, s, sources, h, tile="auto"):
+        F = (1.0 / s).contiguous()
+        phis = solve_batched([(F, src, h) for src in sources], shared_F=True, tile=tile)
+        phi = torch.stack(phis)
+        ctx.save_for_backward(F, phi)
+        ctx.sources, ctx.h, ctx.tile = sources, h, tile
+        return phi
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        F, phi = ctx.saved_tensors
+        rs = [grad_phi[q].contiguous() for q in range(grad_phi.shape[0])]
+        g = adjoint_batched([(F, src, ctx.h) for src in ctx.sources], list(phi.unbind(0)), rs, shared_F=True,
+                            sum_instances=True, tile=ctx.tile)
+        return g, None, None, None

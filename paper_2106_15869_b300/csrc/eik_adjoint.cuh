@@ -1,0 +1,351 @@
+// eik_adjoint.cuh -- adjoint of the discrete Eikonal solve (sm_103a).
+//
+// Not in the paper: the gradient of a loss L(phi) with respect to slowness
+// s = 1/F, by the adjoint-state method (Leung & Qian 2006) applied to the
+// residual of eq. (6) at a non-source node i,
+//   G_i(phi, s) = sum_d ((phi_i - m_{i,d})^+)^2 - h^2 s_i^2 = 0,
+// with m_{i,d} the selected upwind neighbour on axis d (argmin of the two
+// neighbours; on a tie the lower flat index).  With w_{i,d} = 2 (phi_i -
+// m_{i,d})^+ and r = dL/dphi, the adjoint lambda solves J^T lambda = r:
+//   lambda_j J_jj = r_j + sum_{i : m_{i,d} = j} w_{i,d} lambda_i,
+//   J_jj = sum_d w_{j,d},
+// and dL/ds_j = 2 h^2 s_j lambda_j = 2 h tau_j lambda_j (tau = h/F), 0 at
+// sources and at unreachable or impassable nodes.  w_{i,d} > 0 needs phi_i >
+// phi_j, so the dependencies form a DAG oriented against the arrival times:
+// lambda flows from the receivers back toward the sources.
+//
+// GPU form: the same tile machinery as the forward solve.  A listed tile is
+// staged (phi with a two-node face halo, to know whether a neighbour i of j
+// selects j, which needs the neighbour beyond i; lambda with a one-node
+// halo), each node computes its own J_jj and the six weights w_{i->j} of its
+// neighbours once, then lambda is relaxed by Jacobi sweeps inside the tile
+// until nothing changes (exact: on a DAG a value computed from final inputs is
+// final, and the sum has a fixed order, so the result does not depend on the
+// schedule).  Neighbour tiles across faces where lambda changed are listed.
+// Sources keep lambda = 0, so they feed nothing upstream.
+#pragma once
+
+#include "eik_kernels.cuh"
+
+namespace eik {
+
+template <class T>
+struct AdjParams {
+    const InstDesc *desc;       // in_off: F offset; out_off: phi and r offset; aux_off: gradient offset
+    int B;
+    int n_tiles;
+    int *tile_rec;              // [n_tiles][8]: neighbours, instance, unused
+    int *tstamp;
+    int *list0, *list1;
+    T *phi_t, *tau_t, *lam_t, *r_t;
+    Ctl *ctl;
+    long long max_iters;
+    int max_sweeps;
+    const T *F;
+    const T *phi_in;
+    const T *r_in;              // dL/dphi, same offsets as phi
+    const long long *src_idx;
+    long long n_src;
+    T *g_out;
+};
+
+template <int BX, int BY, int BZ>
+struct AdjGeom {
+    using G = TileGeom<BX, BY, BZ>;
+    // phi staged with a two-node halo on every face (edges and corners unused)
+    static constexpr int PX = BX + 4, PY = BY + 4, PZ = BZ + 4;
+    static constexpr int PS = PX * PY * PZ;
+    static __device__ __forceinline__ int pidx(int x, int y, int z) { return ((z + 2) * PY + (y + 2)) * PX + (x + 2); }
+};
+
+template <class T, int BX, int BY, int BZ>
+struct AdjSmem {
+    T phi[AdjGeom<BX, BY, BZ>::PS];
+    T lam[TileGeom<BX, BY, BZ>::S];
+};
+
+// Step 0: bricks of tau, phi, r; lambda = 0; tile records; control block.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX *BY *BZ) k_adj_init(AdjParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    __shared__ int s_b;
+    const int g = blockIdx.x;
+    if (threadIdx.x == 0) s_b = find_inst_by_tile(P.desc, P.B, g);
+    __syncthreads();
+    const InstDesc &d = P.desc[s_b];
+    const long long l = g - d.tile_base;
+    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    const int tid = threadIdx.x;
+    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
+    T tau = Num<T>::inf(), phi = Num<T>::inf(), r = T(0);
+    if (i < d.nx && j < d.ny && k < d.nz) {
+        const long long p = ((long long)k * d.ny + j) * d.nx + i;
+        const T f = P.F[d.in_off + p];
+        if (f > T(0)) tau = T(d.h) / f;
+        phi = P.phi_in[d.out_off + p];
+        r = P.r_in[d.out_off + p];
+        if (!(phi < Num<T>::inf())) r = T(0);      // an unreachable receiver has no gradient
+    }
+    const size_t q = (size_t)g * G::V + tid;
+    P.tau_t[q] = tau;
+    P.phi_t[q] = phi;
+    P.lam_t[q] = T(0);
+    P.r_t[q] = r;
+    if (tid == 0) P.tstamp[g] = 0;
+    if (tid < 8) {
+        int nb;
+        switch (tid) {
+            case 0: nb = tx > 0 ? g - 1 : -1; break;
+            case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
+            case 2: nb = ty > 0 ? g - d.tx : -1; break;
+            case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
+            case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
+            case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
+            case 6: nb = s_b; break;
+            default: nb = 0; break;
+        }
+        P.tile_rec[8 * g + tid] = nb;
+    }
+    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) reinterpret_cast<unsigned *>(P.ctl)[tid] = 0u;
+}
+
+// Sources: tau = -1 marker (lambda stays 0 there).
+template <class T, int BX, int BY, int BZ>
+__global__ void k_adj_sources(AdjParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P.n_src) return;
+    const int b = find_inst_by_src(P.desc, P.B, s);
+    const InstDesc &d = P.desc[b];
+    if (s < d.src_begin || s >= d.src_end) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
+    const long long p = P.src_idx[s];
+    const long long N = (long long)d.nx * d.ny * d.nz;
+    if (p < 0 || p >= N) { atomicOr(&P.ctl->flags, kFlagBadSource); return; }
+    const int i = (int)(p % d.nx), j = (int)((p / d.nx) % d.ny), k = (int)(p / ((long long)d.nx * d.ny));
+    const int g = (int)(d.tile_base + ((long long)(k / BZ) * d.ty + (j / BY)) * d.tx + (i / BX));
+    const int loc = ((k % BZ) * BY + (j % BY)) * BX + (i % BX);
+    P.tau_t[(size_t)g * G::V + loc] = T(-1);
+}
+
+// The initial list: tiles holding a non-source node with r != 0.
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX *BY *BZ) k_adj_seed(AdjParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    const int g = blockIdx.x;
+    const size_t q = (size_t)g * G::V + threadIdx.x;
+    const int want = (P.r_t[q] != T(0) && !(P.tau_t[q] < T(0))) ? 1 : 0;
+    if (__syncthreads_or(want) && threadIdx.x == 0) {
+        P.tstamp[g] = 1;
+        const int pos = atomicAdd(&P.ctl->rcnt[0], 1);
+        if (pos < P.n_tiles) P.list0[pos] = g;
+        else atomicOr(&P.ctl->flags, kFlagOverflow);
+    }
+}
+
+// One visit of tile g by a group of GT threads (one or two nodes each).
+template <class T, int BX, int BY, int BZ>
+__device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, BY, BZ> &sm, const int (&nb)[6], int g,
+                                         int gt, int bid, unsigned &mine, bool &first_changed) {
+    using G = TileGeom<BX, BY, BZ>;
+    using A = AdjGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ>;
+    constexpr int NPT = GG::NPT;
+    const T INF = Num<T>::inf();
+    T lam[NPT], rr[NPT], tau[NPT], J[NPT], w[NPT][6];
+    int x[NPT], y[NPT], z[NPT];
+    // interior
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) {
+        const int q = gt + GG::GT * m;
+        x[m] = q % BX; y[m] = (q / BX) % BY; z[m] = q / (BX * BY);
+        const size_t a = (size_t)g * G::V + q;
+        const T ph = __ldcg(P.phi_t + a);
+        lam[m] = __ldcg(P.lam_t + a);
+        rr[m] = __ldcg(P.r_t + a);
+        tau[m] = __ldcg(P.tau_t + a);
+        sm.phi[A::pidx(x[m], y[m], z[m])] = ph;
+        sm.lam[G::sidx(x[m], y[m], z[m])] = lam[m];
+    }
+    // halos: phi two nodes deep, lambda one node deep, on the six faces
+    constexpr int FX = BY * BZ, FY = BX * BZ, FZ = BX * BY;
+    constexpr int HN = 2 * (FX + FY + FZ);
+    for (int e = gt; e < 2 * HN; e += GG::GT) {
+        const int depth = e / HN;                 // 0: adjacent layer, 1: second layer
+        int f, a, b2, r = e % HN;
+        if (r < 2 * FX) { f = r / FX; r %= FX; a = r % BY; b2 = r / BY; }
+        else if ((r -= 2 * FX) < 2 * FY) { f = 2 + r / FY; r %= FY; a = r % BX; b2 = r / BX; }
+        else { r -= 2 * FY; f = 4 + r / FZ; r %= FZ; a = r % BX; b2 = r / BX; }
+        int sx, sy, sz, lx, ly, lz;                // staged position, node in the neighbour tile
+        const int dd = depth;                      // 0 or 1
+        switch (f) {
+            case 0: sx = -1 - dd; sy = a; sz = b2; lx = BX - 1 - dd; ly = a; lz = b2; break;
+            case 1: sx = BX + dd; sy = a; sz = b2; lx = dd; ly = a; lz = b2; break;
+            case 2: sx = a; sy = -1 - dd; sz = b2; lx = a; ly = BY - 1 - dd; lz = b2; break;
+            case 3: sx = a; sy = BY + dd; sz = b2; lx = a; ly = dd; lz = b2; break;
+            case 4: sx = a; sy = b2; sz = -1 - dd; lx = a; ly = b2; lz = BZ - 1 - dd; break;
+            default: sx = a; sy = b2; sz = BZ + dd; lx = a; ly = b2; lz = dd; break;
+        }
+        const int n = nb[f];
+        // a second layer beyond a one-node-thick tile axis lies two tiles away: not staged (+inf),
+        // which only matters for BZ == 1 tiles, whose grids have no z neighbours at all
+        const bool thin = (f >= 4 && BZ == 1) || (f >= 2 && f < 4 && BY == 1) || (f < 2 && BX == 1);
+        T pv = INF, lv = T(0);
+        if (n >= 0 && !(dd == 1 && thin)) {
+            const size_t src = (size_t)n * G::V + (lz * BY + ly) * BX + lx;
+            pv = __ldcg(P.phi_t + src);
+            if (dd == 0) lv = __ldcg(P.lam_t + src);
+        }
+        sm.phi[A::pidx(sx, sy, sz)] = pv;
+        if (dd == 0) sm.lam[G::sidx(sx, sy, sz)] = lv;
+    }
+    group_sync(bid, GG::GT);
+    // J_jj and the weights w_{i->j} of the six neighbours i = j + e (order -x,+x,-y,+y,-z,+z)
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) {
+        const T pj = sm.phi[A::pidx(x[m], y[m], z[m])];
+        J[m] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[m][k] = T(0);
+        if (tau[m] < T(0) || !(pj < INF) || !(tau[m] < INF)) { J[m] = T(0); continue; }
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+            const T lo1 = sm.phi[A::pidx(x[m] - ex, y[m] - ey, z[m] - ez)];
+            const T hi1 = sm.phi[A::pidx(x[m] + ex, y[m] + ey, z[m] + ez)];
+            const T lo2 = sm.phi[A::pidx(x[m] - 2 * ex, y[m] - 2 * ey, z[m] - 2 * ez)];
+            const T hi2 = sm.phi[A::pidx(x[m] + 2 * ex, y[m] + 2 * ey, z[m] + 2 * ez)];
+            const T mv = vmin(lo1, hi1);
+            if (mv < INF && pj > mv) J[m] += T(2) * (pj - mv);
+            // neighbour i = j - e selects j iff phi_j < phi_{j-2e} (a tie goes to the lower index j-2e)
+            if (lo1 < INF && pj < lo2 && lo1 > pj) w[m][2 * ax] = T(2) * (lo1 - pj);
+            // neighbour i = j + e selects j iff phi_j <= phi_{j+2e} (a tie goes to the lower index j)
+            if (hi1 < INF && pj <= hi2 && hi1 > pj) w[m][2 * ax + 1] = T(2) * (hi1 - pj);
+        }
+    }
+    // Jacobi on lambda until no change; sources and nodes with J == 0 keep lambda
+    mine = 0;
+    first_changed = false;
+    int s = 0;
+    for (;;) {
+        unsigned ch = 0;
+#pragma unroll
+        for (int m = 0; m < NPT; ++m) {
+            if (!(J[m] > T(0))) continue;
+            const int c = G::sidx(x[m], y[m], z[m]);
+            T acc = rr[m];
+            acc += w[m][0] * sm.lam[c - 1];
+            acc += w[m][1] * sm.lam[c + 1];
+            acc += w[m][2] * sm.lam[c - G::SX];
+            acc += w[m][3] * sm.lam[c + G::SX];
+            acc += w[m][4] * sm.lam[c - G::SX * G::SY];
+            acc += w[m][5] * sm.lam[c + G::SX * G::SY];
+            const T nl = acc / J[m];
+            if (nl != lam[m]) { lam[m] = nl; sm.lam[c] = nl; ch |= 1u << m; }
+        }
+        mine |= ch;
+        ++s;
+        const int any = group_sync_or(bid, GG::GT, ch != 0);
+        if (s == 1) first_changed = any != 0;
+        if (!any || s >= P.max_sweeps) break;
+    }
+#pragma unroll
+    for (int m = 0; m < NPT; ++m)
+        if (mine >> m & 1) __stcg(P.lam_t + (size_t)g * G::V + gt + GG::GT * m, lam[m]);
+    return s;
+}
+
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ>;
+    extern __shared__ __align__(16) unsigned char adj_smem_raw[];
+    AdjSmem<T, BX, BY, BZ> *sms = reinterpret_cast<AdjSmem<T, BX, BY, BZ> *>(adj_smem_raw);
+    __shared__ int s_n;
+    __shared__ int s_tile[GG::NG];
+    __shared__ int s_nb[GG::NG][6];
+    __shared__ int s_fmask[GG::NG];
+    const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
+    AdjSmem<T, BX, BY, BZ> &sm = sms[gi];
+    // faces that never get loaded stay +inf / 0 (z of 2D tiles, far corners)
+    for (int q = gt; q < AdjGeom<BX, BY, BZ>::PS; q += GG::GT) sm.phi[q] = Num<T>::inf();
+    for (int q = gt; q < G::S; q += GG::GT) sm.lam[q] = T(0);
+    Ctl *ctl = P.ctl;
+    unsigned long long target = 0;
+    long long tiles = 0, sweeps = 0;
+    const int groups = gridDim.x * GG::NG;
+    int r = 0;
+    __syncthreads();
+    for (;; ++r) {
+        if (threadIdx.x == 0) s_n = ld_volatile(&ctl->rcnt[r % 3]);
+        __syncthreads();
+        const int n = min(s_n, P.n_tiles);
+        if (n == 0) break;
+        if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); break; }
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rcnt[(r + 2) % 3] = 0;
+        const int nslot = (r + 1) % 3;
+        const int *in = (r & 1) ? P.list1 : P.list0;
+        int *out = (r & 1) ? P.list0 : P.list1;
+        const int next_stamp = r + 2;
+        for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
+            group_sync(bid, GG::GT);
+            if (gt == 0) {
+                const int g = __ldcg(in + idx);
+                s_tile[gi] = g;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) s_nb[gi][f] = __ldcg(P.tile_rec + 8 * g + f);
+                s_fmask[gi] = 0;
+            }
+            group_sync(bid, GG::GT);
+            const int g = s_tile[gi];
+            int nb[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
+            unsigned mine;
+            bool changed;
+            const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
+            if (gt == 0) { tiles++; sweeps += s; }
+#pragma unroll
+            for (int m = 0; m < GG::NPT; ++m)
+                if (mine >> m & 1) {
+                    const int fb = G::faces_of(gt + GG::GT * m);
+                    if (fb) atomicOr(&s_fmask[gi], fb);
+                }
+            group_sync(bid, GG::GT);
+            if (gt < 32) {
+                const int fm = s_fmask[gi];
+                int cand = -1;
+                if (gt < 6 && (fm >> gt & 1)) cand = nb[gt];
+                if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+                const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand);
+            }
+        }
+        if (!grid_sync(ctl, target)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters_remedy = r;
+    if (threadIdx.x == 0) {
+        if (tiles) atomicAdd((unsigned long long *)&ctl->tiles_remedy, (unsigned long long)tiles);
+        if (sweeps) atomicAdd((unsigned long long *)&ctl->sweeps, (unsigned long long)sweeps);
+    }
+}
+
+// g_out[instance][node] += 2 h tau lambda at non-source nodes with finite phi and tau
+// (atomic: instances may share one gradient array).
+template <class T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX *BY *BZ) k_adj_output(AdjParams<T> P) {
+    using G = TileGeom<BX, BY, BZ>;
+    const int g = blockIdx.x;
+    const int b = P.tile_rec[8 * g + 6];
+    const InstDesc &d = P.desc[b];
+    const long long l = g - d.tile_base;
+    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    const int tid = threadIdx.x;
+    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
+    if (i >= d.nx || j >= d.ny || k >= d.nz) return;
+    const size_t q = (size_t)g * G::V + tid;
+    const T lam = P.lam_t[q], tau = P.tau_t[q], phi = P.phi_t[q];
+    if (lam == T(0) || tau < T(0) || !(tau < Num<T>::inf()) || !(phi < Num<T>::inf())) return;
+    atomicAdd(P.g_out + d.aux_off + ((long long)k * d.ny + j) * d.nx + i, T(2) * T(d.h) * tau * lam);
+}
+
+}  // namespace eik

@@ -14,6 +14,7 @@
 #include "eik_common.cuh"
 #include "eik_kernels.cuh"
 #include "eik_async.cuh"
+#include "eik_adjoint.cuh"
 
 using namespace eik;
 
@@ -191,7 +192,7 @@ int upload_desc(InstDesc *ddesc, double *inst_acc, const std::vector<InstDesc> &
         c.first = first;
         c.count = std::min(kMaxInstPerLaunch, B - first);
         for (int q = 0; q < c.count; ++q) c.d[q] = h[(size_t)(first + q)];
-        k_write_desc<<<1, kMaxInstPerLaunch, 0, st>>>(ddesc, inst_acc, c);
+        k_write_desc<<<1, kMaxInstPerLaunch, 0, st>>>(ddesc, inst_acc, c);   // inst_acc may be NULL
         EIK_CUDA(cudaGetLastError(), "k_write_desc launch");
     }
     return EIK_OK;
@@ -455,6 +456,152 @@ int solve_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F
     return dispatch_tile<float>(L, o, w, F, src_idx, src_val, n_src, phi, st, stats);
 }
 
+// ---------------------------------------------------------------- adjoint
+struct AdjLayout {
+    size_t ctl, desc, tile_rec, tstamp, list0, list1, phi_t, tau_t, lam_t, r_t, total;
+    long long n_tiles;
+    std::vector<InstDesc> desc_host;
+};
+
+bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout &L, std::string *why) {
+    Layout fl;   // reuse the forward's dims/tile checks and descriptors
+    if (!make_layout(B, grids, o, fl, why)) return false;
+    const TileShape ts = tile_shape(o.tile);
+    const size_t esz = o.precision == EIK_FP64 ? 8 : 4;
+    const long long V = (long long)ts.bx * ts.by * ts.bz;
+    L.desc_host = fl.desc_host;
+    L.n_tiles = fl.n_tiles;
+    const long long tiles = fl.n_tiles;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
+    L.ctl = take(sizeof(Ctl));
+    L.desc = take(sizeof(InstDesc) * (size_t)B);
+    L.tile_rec = take(4 * 8 * (size_t)tiles);
+    L.tstamp = take(4 * (size_t)tiles);
+    L.list0 = take(4 * (size_t)tiles);
+    L.list1 = take(4 * (size_t)tiles);
+    L.phi_t = take(esz * (size_t)(tiles * V));
+    L.tau_t = take(esz * (size_t)(tiles * V));
+    L.lam_t = take(esz * (size_t)(tiles * V));
+    L.r_t = take(esz * (size_t)(tiles * V));
+    L.total = off;
+    return true;
+}
+
+template <class T, int BX, int BY, int BZ>
+int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, const void *phi, const int64_t *src_idx,
+                int64_t n_src, const void *r, void *g, cudaStream_t st, eik_stats *stats) {
+    using GG = GroupGeom<BX, BY, BZ>;
+    AdjParams<T> P;
+    P.desc = reinterpret_cast<const InstDesc *>(ws + L.desc);
+    P.B = (int)L.desc_host.size();
+    P.n_tiles = (int)L.n_tiles;
+    P.tile_rec = reinterpret_cast<int *>(ws + L.tile_rec);
+    P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
+    P.list0 = reinterpret_cast<int *>(ws + L.list0);
+    P.list1 = reinterpret_cast<int *>(ws + L.list1);
+    P.phi_t = reinterpret_cast<T *>(ws + L.phi_t);
+    P.tau_t = reinterpret_cast<T *>(ws + L.tau_t);
+    P.lam_t = reinterpret_cast<T *>(ws + L.lam_t);
+    P.r_t = reinterpret_cast<T *>(ws + L.r_t);
+    P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
+    long long m = 0;
+    for (const InstDesc &d : L.desc_host) m = std::max(m, (long long)d.tx + d.ty + d.tz);
+    P.max_iters = o.max_iters > 0 ? o.max_iters : 64 * m + 4096;
+    P.max_sweeps = 4 * (BX + BY + BZ) + 8;
+    P.F = static_cast<const T *>(F);
+    P.phi_in = static_cast<const T *>(phi);
+    P.r_in = static_cast<const T *>(r);
+    P.src_idx = reinterpret_cast<const long long *>(src_idx);
+    P.n_src = n_src;
+    P.g_out = static_cast<T *>(g);
+    constexpr int V = BX * BY * BZ;
+    PhaseEvents pe;
+    int rc = EIK_OK;
+    if (stats && (rc = pe.create())) return rc;
+    pe.record(0, st);
+    rc = upload_desc(const_cast<InstDesc *>(P.desc), nullptr, L.desc_host, st);
+    if (rc) return rc;
+    k_adj_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_adj_init launch");
+    if (n_src > 0) {
+        k_adj_sources<T, BX, BY, BZ><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(P);
+        EIK_CUDA(cudaGetLastError(), "k_adj_sources launch");
+    }
+    k_adj_seed<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_adj_seed launch");
+    DevInfo di;
+    rc = device_info(di);
+    if (rc) return rc;
+    constexpr int CTA = 32 * kWarpsPerCta;
+    const size_t dsm = sizeof(AdjSmem<T, BX, BY, BZ>) * GG::NG;
+    int per_sm = 0;
+    EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<T, BX, BY, BZ>, CTA, dsm),
+             "occupancy query");
+    if (!di.coop || per_sm < 1) return fail(EIK_ERR_CUDA, "the adjoint needs a cooperative launch");
+    int grid = per_sm * di.sms;
+    const int need = (int)((L.n_tiles + GG::NG - 1) / GG::NG);
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    pe.record(1, st);
+    void *args[] = {&P};
+    EIK_CUDA(cudaLaunchCooperativeKernel((const void *)k_adj_persistent<T, BX, BY, BZ>, dim3(grid), dim3(CTA), args,
+                                         dsm, st),
+             "cooperative launch");
+    pe.record(2, st);
+    k_adj_output<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_adj_output launch");
+    pe.record(3, st);
+    if (stats) return finish_stats(P.ctl, st, stats, &pe);
+    return EIK_OK;
+}
+
+int adjoint_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F_offsets, const void *phi,
+                 const int64_t *phi_offsets, const int64_t *src_idx, const int64_t *src_offsets, const void *r,
+                 void *g, const int64_t *g_offsets, void *ws, size_t ws_bytes, void *stream, const eik_options *opt,
+                 eik_stats *stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (B < 1 || B > (1ll << 24)) return fail(EIK_ERR_ARG, "batch size must be in [1, 2^24]");
+    if (!grids || !F_offsets || !phi_offsets || !src_offsets || !g_offsets)
+        return fail(EIK_ERR_ARG, "grids and offset arrays must be non-NULL");
+    Opts o;
+    if (!read_opts(opt, B, grids, o)) return fail(EIK_ERR_ARG, "invalid options");
+    AdjLayout L;
+    std::string why;
+    if (!make_adj_layout(B, grids, o, L, &why)) return fail(EIK_ERR_ARG, "%s", why.c_str());
+    if (!ws) return fail(EIK_ERR_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(EIK_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total) return fail(EIK_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+    if (!F || !phi || !r || !g) return fail(EIK_ERR_ARG, "F, phi, r and g must be non-NULL");
+    if (src_offsets[0] != 0) return fail(EIK_ERR_ARG, "src_offsets[0] must be 0");
+    for (int64_t b = 0; b < B; ++b) {
+        if (src_offsets[b + 1] < src_offsets[b]) return fail(EIK_ERR_ARG, "src_offsets must be non-decreasing");
+        if (F_offsets[b] < 0 || phi_offsets[b] < 0 || g_offsets[b] < 0) return fail(EIK_ERR_ARG, "offsets must be >= 0");
+        InstDesc &d = L.desc_host[(size_t)b];
+        d.in_off = F_offsets[b];
+        d.out_off = phi_offsets[b];
+        d.aux_off = g_offsets[b];
+        d.src_begin = src_offsets[b];
+        d.src_end = src_offsets[b + 1];
+    }
+    const int64_t n_src = src_offsets[B];
+    if (n_src > 0 && !src_idx) return fail(EIK_ERR_ARG, "src_idx must be non-NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(ws);
+#define EIK_ADJ_DISPATCH(T)                                                                                       \
+    switch (o.tile) {                                                                                             \
+        case EIK_TILE_4x4x4: return run_adjoint<T, 4, 4, 4>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats);    \
+        case EIK_TILE_8x8x4: return run_adjoint<T, 8, 8, 4>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats);    \
+        case EIK_TILE_16x16x1: return run_adjoint<T, 16, 16, 1>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats); \
+        case EIK_TILE_8x4x4: return run_adjoint<T, 8, 4, 4>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats);    \
+        case EIK_TILE_8x8x1: return run_adjoint<T, 8, 8, 1>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats);    \
+        default: return run_adjoint<T, 8, 8, 8>(L, o, w, F, phi, src_idx, n_src, r, g, st, stats);                \
+    }
+    if (o.precision == EIK_FP64) { EIK_ADJ_DISPATCH(double) }
+    EIK_ADJ_DISPATCH(float)
+#undef EIK_ADJ_DISPATCH
+}
+
 // ---------------------------------------------------------------- no-allocation variant
 // Fixed scratch for eik_solve_noalloc: a file-scope device array, so a caller
 // that may not allocate device memory still gets a workspace.  Every device
@@ -536,6 +683,34 @@ int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_id
     // block, per-tile state, keys, lists), so stale contents of the shared
     // array from an earlier call do not matter
     return eik_solve(grid, F, src_idx, src_val, n_src, phi, scratch, kNoAllocScratchBytes, stream, opt, stats);
+}
+
+size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt) {
+    if (B < 1 || !grids) return 0;
+    Opts o;
+    if (!read_opts(opt, B, grids, o)) return 0;
+    AdjLayout L;
+    if (!make_adj_layout(B, grids, o, L, nullptr)) return 0;
+    return L.total;
+}
+
+int eik_adjoint_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,
+                        const void *phi_packed, const int64_t *phi_offsets, const int64_t *src_idx,
+                        const int64_t *src_offsets, const void *r_packed, void *g_packed, const int64_t *g_offsets,
+                        void *workspace, size_t workspace_bytes, void *stream, const eik_options *opt,
+                        eik_stats *stats) {
+    return adjoint_impl(B, grids, F_packed, F_offsets, phi_packed, phi_offsets, src_idx, src_offsets, r_packed,
+                        g_packed, g_offsets, workspace, workspace_bytes, stream, opt, stats);
+}
+
+int eik_adjoint(const eik_grid *grid, const void *F, const void *phi, const int64_t *src_idx, int64_t n_src,
+                const void *r, void *g, void *workspace, size_t workspace_bytes, void *stream,
+                const eik_options *opt, eik_stats *stats) {
+    if (n_src < 0) return fail(EIK_ERR_ARG, "n_src must be >= 0");
+    const int64_t zero = 0;
+    const int64_t so[2] = {0, n_src};
+    return adjoint_impl(1, grid, F, &zero, phi, &zero, src_idx, so, r, g, &zero, workspace, workspace_bytes, stream,
+                        opt, stats);
 }
 
 const char *eik_last_error(void) { return g_err.c_str(); }

@@ -40,6 +40,7 @@ struct InstDesc {
     int64_t out_off;              // element offset of phi (and of g in the adjoint)
     int64_t src_begin, src_end;   // entries of the packed source arrays
     double h;
+    int64_t aux_off;              // element offset of the adjoint's gradient output
 };
 
 struct DescChunk {                // by-value kernel parameter (capture-safe upload)

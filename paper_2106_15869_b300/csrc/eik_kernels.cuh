@@ -22,6 +22,7 @@ __global__ void k_write_desc(InstDesc *desc, double *inst_acc, DescChunk chunk) 
     const int i = threadIdx.x;
     if (i < chunk.count) {
         desc[chunk.first + i] = chunk.d[i];
+        if (!inst_acc) return;
         double *a = inst_acc + 4 * (chunk.first + i);
         a[0] = 0.0;                                   // sum of F over passable nodes
         a[1] = 0.0;                                   // their count

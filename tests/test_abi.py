@@ -32,7 +32,8 @@ def test_library_builds_and_loads():
 def test_every_declared_symbol_is_exported():
     lib = _lib.load()
     names = _declared_functions()
-    assert {"eik_solve", "eik_solve_batched", "eik_workspace_size", "eik_last_error"} <= names
+    assert {"eik_solve", "eik_solve_batched", "eik_workspace_size", "eik_last_error", "eik_adjoint",
+            "eik_adjoint_batched", "eik_adjoint_workspace_size_batched", "eik_solve_noalloc"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
