@@ -40,6 +40,9 @@ LOOP_BYTES_PER_NODE = 20
 # the loop (20 B), unpack read + write (8 B)
 STEP_BYTES_PER_NODE = 40
 FALLBACK_HBM_GBS = 6400.0
+# kernels of one default solve: k_write_desc, k_init, k_scale, k_tile_scale, k_sources,
+# k_persistent, k_unpack
+LAUNCHES_PER_SOLVE = 7
 
 # DRAM traffic of one k_persistent launch on the default workload, from an
 # ncu capture (profiles/); valid only while the kernel sources hash matches.
@@ -285,10 +288,18 @@ def run_ours(args, ws, rank, local):
                        "l2": "flushed between steps (256 MiB write outside the per-step events)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": LAUNCHES_PER_SOLVE * args.steps,
             "solver_stats": {k: s0[k] for k in ("iters_update", "iters_remedy", "tiles_update",
                                                 "tiles_flagged", "tiles_remedy", "sweeps", "tiles_deferred")},
             "wall_s_timed_region": wall, "kernel_source_hash": src_hash}
+    # where the loop time goes (per-iteration trace of one more solve, outside the timed region)
+    if len(insts) == 1:
+        with api.Trace() as tr:
+            step(stats=False)
+        line["trace"] = tr.summary()
+    if not args.no_extras:
+        line["batched"] = bench_batched(args, dev, wsp, flush_buf)
+        line["adjoint"] = bench_adjoint(args, dev, wsp, flush_buf)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import numpy as np
         import oracle
@@ -306,6 +317,74 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+def _timed(fn, flush_buf, reps):
+    """Median device time (ms) of fn() over reps runs, L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        flush_buf.zero_()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    return statistics.median(ms)
+
+
+def bench_batched(args, dev, wsp, flush_buf):
+    """64 lognormal instances (edges 64..192): one batched solve vs one solve per instance."""
+    import torch
+    from paper_2106_15869_b300 import api, workloads as W
+    insts = W.lognormal_batch(64)
+    n = sum(i.n_nodes for i in insts)
+    probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h) for i in insts]
+    batched = lambda: api.solve_batched(probs, workspace=wsp)
+    plain = lambda: [api.solve(p[0], p[1], p[2], workspace=wsp) for p in probs]
+    batched(); plain()
+    tb = _timed(batched, flush_buf, 3)
+    tp = _timed(plain, flush_buf, 2)
+    _, st = api.solve_batched(probs, workspace=wsp, return_stats=True)
+    return {"workload": "lognormal_batch64 (64 instances, edges 64..192, F = exp(0.3 g))", "nodes": n,
+            "batched_ms": tb, "batched_nodes_per_s": n / (tb / 1e3), "plain_loop_ms": tp,
+            "plain_loop_nodes_per_s": n / (tp / 1e3), "speedup_vs_plain": tp / tb,
+            "loop_ms": st["ms_loop"], "loop_gbs_algorithmic": LOOP_BYTES_PER_NODE * n / (st["ms_loop"] / 1e3) / 1e9}
+
+
+def bench_adjoint(args, dev, wsp, flush_buf):
+    """Tomography 192^3, 16 shots, 256 receivers: forward (one batched solve of the 16 shots on one
+    slowness model) + adjoint (one batched adjoint, gradients summed) vs the forward alone and vs 16
+    plain single solves."""
+    import torch
+    from paper_2106_15869_b300 import api, workloads as W
+    t = W.tomography_3d(192)
+    F = torch.as_tensor(1.0 / t["s_init"], dtype=torch.float32).to(dev)
+    shots = [[int(s)] for s in t["sources"]]
+    rec = torch.as_tensor(t["receivers"]).to(dev)
+    probs = [(F, sh, t["h"]) for sh in shots]
+    phis = api.solve_batched(probs, shared_F=True, workspace=wsp)
+    rs = []
+    for ph in phis:
+        r = torch.zeros_like(ph).reshape(-1)
+        r[rec] = 1.0
+        rs.append(r.view(ph.shape))
+    fwd = lambda: api.solve_batched(probs, shared_F=True, workspace=wsp)
+    adj = lambda: api.adjoint_batched(probs, phis, rs, shared_F=True, sum_instances=True, workspace=wsp)
+    both = lambda: (fwd(), adj())
+    plain = lambda: [api.solve(F, sh, t["h"], workspace=wsp) for sh in shots]
+    both(); plain()
+    tf = _timed(fwd, flush_buf, 3)
+    ta = _timed(adj, flush_buf, 3)
+    tb = _timed(both, flush_buf, 3)
+    tp = _timed(plain, flush_buf, 2)
+    n = F.numel() * len(shots)
+    return {"workload": "tomography 192^3, 16 shots, 256 receivers", "nodes_per_pass": n,
+            "forward_ms": tf, "adjoint_ms": ta, "forward_plus_adjoint_ms": tb,
+            "fwd_adj_over_fwd": tb / tf, "plain_16_solves_ms": tp, "forward_speedup_vs_plain": tp / tf,
+            "forward_nodes_per_s": n / (tf / 1e3), "fwd_adj_nodes_per_s": n / (tb / 1e3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,6 +399,7 @@ def main():
     ap.add_argument("--order", type=float, default=0.0,
                     help="list order: 0 default bucketed, >0 bucket width, <0 unordered")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -204,6 +204,18 @@ int eik_adjoint(const eik_grid *grid, const void *F, const void *phi, const int6
 int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_idx, const void *src_val,
                       int64_t n_src, void *phi, void *stream, const eik_options *opt, eik_stats *stats);
 
+/*
+ * Diagnostics: per-iteration trace of the persistent schedule on the current
+ * device.  While a buffer is set, every solve on that device writes into it:
+ * buf[0] = number of records, then records of 4 uint64 = {globaltimer ns,
+ * phase (0 start, 1 Step-2 iteration, 2 Step-3 seed pass, 3 remedy iteration),
+ * list size, tiles visited}, one after each iteration's barrier, up to
+ * `capacity` records (the buffer needs 4*capacity + 1 uint64, device memory,
+ * 8-byte aligned).  Pass NULL to stop tracing.  Not synchronised with running
+ * solves: set it between them.
+ */
+int eik_set_trace(void *device_buffer, int64_t capacity);
+
 /* thread-local message describing the last non-zero return (never NULL) */
 const char *eik_last_error(void);
 

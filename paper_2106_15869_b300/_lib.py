@@ -95,6 +95,9 @@ def _optional_symbols(lib):
     G = ctypes.POINTER(eik_grid)
     O = ctypes.POINTER(eik_options)
     S = ctypes.POINTER(eik_stats)
+    if hasattr(lib, "eik_set_trace"):
+        lib.eik_set_trace.restype = ctypes.c_int
+        lib.eik_set_trace.argtypes = [_vp, _i64]
     if hasattr(lib, "eik_solve_noalloc"):
         lib.eik_solve_noalloc.restype = ctypes.c_int
         lib.eik_solve_noalloc.argtypes = [G, _vp, _vp, _vp, _i64, _vp, _vp, O, S]

@@ -285,3 +285,50 @@ class EikonalFn(torch.autograd.Function):
         g = adjoint_batched([(F, src, ctx.h) for src in ctx.sources], list(phi.unbind(0)), rs, shared_F=True,
                             sum_instances=True, tile=ctx.tile)
         return g, None, None, None
+
+
+class Trace:
+    """Context manager: per-iteration trace of the solves run inside it.
+
+        with api.Trace() as tr:
+            api.solve(...)
+        tr.records   # numpy (n, 4): time ns, phase, list size, tiles visited
+    """
+
+    def __init__(self, capacity: int = 1 << 16, device=None):
+        self.capacity = int(capacity)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buf = None
+        self.records = None
+
+    def __enter__(self):
+        self.buf = torch.zeros(4 * self.capacity + 1, dtype=torch.int64, device=self.device)
+        with torch.cuda.device(self.device):
+            torch.cuda.synchronize()
+            _lib.check(_lib.load().eik_set_trace(self.buf.data_ptr(), self.capacity))
+        return self
+
+    def __exit__(self, *exc):
+        with torch.cuda.device(self.device):
+            torch.cuda.synchronize()
+            _lib.check(_lib.load().eik_set_trace(None, 0))
+        b = self.buf.cpu().numpy()
+        n = int(b[0])
+        self.records = b[1:1 + 4 * n].reshape(n, 4).astype(np.int64)
+        return False
+
+    def summary(self) -> dict:
+        """Time per phase and per-iteration statistics (microseconds)."""
+        r = self.records
+        if r is None or len(r) < 2:
+            return {}
+        dt = np.diff(r[:, 0]) / 1e3
+        ph = r[1:, 1]
+        out = {}
+        for p, name in ((1, "update"), (2, "seed"), (3, "remedy")):
+            m = ph == p
+            if m.any():
+                out[name] = dict(iterations=int(m.sum()), total_us=float(dt[m].sum()),
+                                 median_us=float(np.median(dt[m])), mean_list=float(r[1:, 2][m].mean()),
+                                 visited=int(r[1:, 3][m].sum()))
+        return out

@@ -185,7 +185,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             case 4: sx = a; sy = b2; sz = -1 - dd; lx = a; ly = b2; lz = BZ - 1 - dd; break;
             default: sx = a; sy = b2; sz = BZ + dd; lx = a; ly = b2; lz = dd; break;
         }
-        const int n = nb[f];
+        const int n = (unsigned)nb[f] < (unsigned)P.n_tiles ? nb[f] : -1;
         // a second layer beyond a one-node-thick tile axis lies two tiles away: not staged (+inf),
         // which only matters for BZ == 1 tiles, whose grids have no z neighbours at all
         const bool thin = (f >= 4 && BZ == 1) || (f >= 2 && f < 4 && BY == 1) || (f < 2 && BX == 1);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
             if (gt < 32) {
                 const int fm = s_fmask[gi];
                 int cand = -1;
-                if (gt < 6 && (fm >> gt & 1)) cand = nb[gt];
+                if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
                 if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
                 const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
                 warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand);

@@ -97,7 +97,7 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
 
 // workspace regions (byte offsets), all 256-byte aligned
 struct Layout {
-    size_t ctl, desc, inst_acc, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t;
+    size_t ctl, desc, tile_fstat, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t;
     size_t q_data, q_seq, q_state, total;
     long long n_tiles;
     unsigned long long q_slots;
@@ -139,10 +139,10 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
     L.ctl = take(sizeof(Ctl));
     L.desc = take(sizeof(InstDesc) * (size_t)B);
-    L.inst_acc = take(4 * sizeof(double) * (size_t)B);
     L.inst_scale = take(sizeof(float) * (size_t)B);
     L.tile_inst = take(4 * (size_t)tiles);
     L.tile_nb = take(4 * 8 * (size_t)tiles);
+    L.tile_fstat = take(16 * (size_t)tiles);
     L.tstate = take(4 * (size_t)tiles);
     L.tstamp = take(4 * (size_t)tiles);
     L.tkey = take(2 * 4 * (size_t)tiles);
@@ -184,7 +184,7 @@ int device_info(DevInfo &di) {
     return EIK_OK;
 }
 
-int upload_desc(InstDesc *ddesc, double *inst_acc, const std::vector<InstDesc> &h, cudaStream_t st) {
+int upload_desc(InstDesc *ddesc, const std::vector<InstDesc> &h, cudaStream_t st) {
     const int B = (int)h.size();
     for (int first = 0; first < B; first += kMaxInstPerLaunch) {
         DescChunk c;
@@ -192,7 +192,7 @@ int upload_desc(InstDesc *ddesc, double *inst_acc, const std::vector<InstDesc> &
         c.first = first;
         c.count = std::min(kMaxInstPerLaunch, B - first);
         for (int q = 0; q < c.count; ++q) c.d[q] = h[(size_t)(first + q)];
-        k_write_desc<<<1, kMaxInstPerLaunch, 0, st>>>(ddesc, inst_acc, c);   // inst_acc may be NULL
+        k_write_desc<<<1, kMaxInstPerLaunch, 0, st>>>(ddesc, c);
         EIK_CUDA(cudaGetLastError(), "k_write_desc launch");
     }
     return EIK_OK;
@@ -257,7 +257,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
     P.tkey = reinterpret_cast<unsigned *>(ws + L.tkey);
     P.inst_scale = reinterpret_cast<float *>(ws + L.inst_scale);
-    P.inst_acc = reinterpret_cast<double *>(ws + L.inst_acc);
+    P.tile_fstat = reinterpret_cast<float *>(ws + L.tile_fstat);
     P.ordered = o.order > 0.0f ? 1 : 0;
     P.order = o.order;
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
@@ -281,12 +281,13 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     int rc = EIK_OK;
     if (stats && (rc = pe.create())) return rc;
     pe.record(0, st);
-    rc = upload_desc(const_cast<InstDesc *>(P.desc), P.inst_acc, L.desc_host, st);
+    rc = upload_desc(const_cast<InstDesc *>(P.desc), L.desc_host, st);
     if (rc) return rc;
     k_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
     EIK_CUDA(cudaGetLastError(), "k_init launch");
     if (P.ordered) {
-        k_scale<BX, BY, BZ><<<(P.B + 127) / 128, 128, 0, st>>>(P.desc, P.inst_acc, P.inst_scale, P.B, P.order);
+        k_scale<BX, BY, BZ><<<P.B, 256, 0, st>>>(P.desc, reinterpret_cast<const float4 *>(P.tile_fstat), P.inst_scale,
+                                                 P.B, P.order);
         EIK_CUDA(cudaGetLastError(), "k_scale launch");
         k_tile_scale<<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P.tile_nb, P.inst_scale,
                                                                                                (int)L.n_tiles);
@@ -520,7 +521,7 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     int rc = EIK_OK;
     if (stats && (rc = pe.create())) return rc;
     pe.record(0, st);
-    rc = upload_desc(const_cast<InstDesc *>(P.desc), nullptr, L.desc_host, st);
+    rc = upload_desc(const_cast<InstDesc *>(P.desc), L.desc_host, st);
     if (rc) return rc;
     k_adj_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
     EIK_CUDA(cudaGetLastError(), "k_adj_init launch");
@@ -683,6 +684,16 @@ int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_id
     // block, per-tile state, keys, lists), so stale contents of the shared
     // array from an earlier call do not matter
     return eik_solve(grid, F, src_idx, src_val, n_src, phi, scratch, kNoAllocScratchBytes, stream, opt, stats);
+}
+
+int eik_set_trace(void *device_buffer, int64_t capacity) {
+    if (capacity < 0 || (device_buffer && capacity < 1)) return fail(EIK_ERR_ARG, "invalid trace capacity");
+    if (device_buffer && reinterpret_cast<uintptr_t>(device_buffer) % 8) return fail(EIK_ERR_ARG, "trace buffer must be 8-byte aligned");
+    unsigned long long *p = static_cast<unsigned long long *>(device_buffer);
+    long long cap = device_buffer ? (long long)capacity : 0;
+    EIK_CUDA(cudaMemcpyToSymbol(g_trace_buf, &p, sizeof(p)), "cudaMemcpyToSymbol(trace)");
+    EIK_CUDA(cudaMemcpyToSymbol(g_trace_cap, &cap, sizeof(cap)), "cudaMemcpyToSymbol(trace)");
+    return EIK_OK;
 }
 
 size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt) {

@@ -152,7 +152,8 @@ __device__ void async_update_phase(const FwdParams<T> &P, const AsyncQ &Q, T *sm
     for (;;) {
         const int g = q_pop(ctl, Q);
         if (g < 0) break;
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        if ((unsigned)nbf >= (unsigned)P.n_tiles) nbf = -1;
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
@@ -187,7 +188,8 @@ __device__ void async_remedy_phase(const FwdParams<T> &P, const AsyncQ &Q, T *sm
     for (;;) {
         const int g = q_pop(ctl, Q);
         if (g < 0) break;
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        if ((unsigned)nbf >= (unsigned)P.n_tiles) nbf = -1;
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
@@ -215,7 +217,8 @@ __device__ void async_detect_pass(const FwdParams<T> &P, const AsyncQ &Q, T *sm,
     Ctl *ctl = P.ctl;
     const int lane = lane_id();
     for (int g = warp_global(); g < P.n_tiles; g += warps_total()) {
-        const int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        int nbf = lane < 6 ? __ldcg(P.tile_nb + 8 * g + lane) : -1;
+        if ((unsigned)nbf >= (unsigned)P.n_tiles) nbf = -1;
         T v[G::NPL], tau[G::NPL];
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         bool low = false;

@@ -44,7 +44,7 @@ struct FwdParams {
     int *tstamp;
     unsigned *tkey;              // [2][n_tiles] encoded list keys (ordered schedule)
     float *inst_scale;           // [B] 1/delta of each instance (ordered schedule)
-    double *inst_acc;            // [B][2] sum of F and count of F > 0 (for delta)
+    float *tile_fstat;           // [n_tiles][4] sum, count, min, max of the passable speeds (for delta)
     int ordered;                 // 1 = bucketed order of the lists
     float order;                 // bucket width in tile-crossing times
     int *list0, *list1;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void stage_tile(const FwdParams<T> &P, T *sm, int g, 
         const int n = __shfl_sync(kFull, nbf, f);
         if (h < G::HALO_LOADED) {
             T hv = Num<T>::inf();
-            if (n >= 0) hv = __ldcg(P.phi_t + (size_t)n * G::V + src);
+            if ((unsigned)n < (unsigned)P.n_tiles) hv = __ldcg(P.phi_t + (size_t)n * G::V + src);
             sm[slot] = hv;
         }
     }
@@ -334,7 +334,8 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
             warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, lane == 0, g, ord.on ? &ctl->kmin[nslot] : nullptr, key);
         } else {
             if (lane == 0) __stcg(P.tstate + g, (int)kSource);                    // Active -> Source
-            const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
+            const int prev = (unsigned)nbf < (unsigned)P.n_tiles ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive)
+                                                                 : (int)kSource;
             const bool act = prev == (int)kDistant;
             unsigned kf = kKeyInf;
             if (ord.on) {
@@ -448,7 +449,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         // `lane` when a node on that face dropped; lane 6 re-lists the tile
         // itself when the sweep cap stopped the relaxation early.
         int cand = -1;
-        if (lane < 6 && (fm >> lane & 1)) cand = nbf;
+        if (lane < 6 && (fm >> lane & 1) && (unsigned)nbf < (unsigned)P.n_tiles) cand = nbf;
         if (lane == 6 && changed && s >= P.max_sweeps) cand = g;
         unsigned kc = kKeyInf;
         if (ord.on) {

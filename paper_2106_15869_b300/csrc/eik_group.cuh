@@ -69,7 +69,7 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
         int f, slot, src;
         G::halo_of(h, f, slot, src);
         const int n = gc.nb[f];
-        sm[slot] = n >= 0 ? __ldcg(P.phi_t + (size_t)n * G::V + src) : Num<T>::inf();
+        sm[slot] = (unsigned)n < (unsigned)P.n_tiles ? __ldcg(P.phi_t + (size_t)n * G::V + src) : Num<T>::inf();
     }
     group_sync(bid, GG::GT);
     mine = 0;
@@ -176,7 +176,7 @@ __device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gc
         }
         if (gt < 32) {
             if (gt == 0) __stcg(P.tstate + g, (int)kSource);
-            const int nbf = gt < 6 ? gc.nb[gt] : -1;
+            const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
             const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
             const bool act = prev == (int)kDistant;
             unsigned kf = kKeyInf;
@@ -248,7 +248,7 @@ __device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gc
         if (gt < 32) {
             const int fm = gc.fmask;
             int cand = -1;
-            if (gt < 6 && (fm >> gt & 1)) cand = gc.nb[gt];
+            if (gt < 6 && (fm >> gt & 1) && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles) cand = gc.nb[gt];
             if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
             unsigned kc = kKeyInf;
             if (ord.on && cand >= 0) {

@@ -16,41 +16,75 @@ namespace eik {
 // latency mode when the list holds at most this many tiles per thread group
 constexpr int kGroupModeFactor = 2;
 
-// ---------------------------------------------------------------- kernels
-// Descriptor upload (by-value parameter, so that the call can be captured).
-__global__ void k_write_desc(InstDesc *desc, double *inst_acc, DescChunk chunk) {
-    const int i = threadIdx.x;
-    if (i < chunk.count) {
-        desc[chunk.first + i] = chunk.d[i];
-        if (!inst_acc) return;
-        double *a = inst_acc + 4 * (chunk.first + i);
-        a[0] = 0.0;                                   // sum of F over passable nodes
-        a[1] = 0.0;                                   // their count
-        reinterpret_cast<unsigned *>(a + 2)[0] = 0x7f800000u;   // min F (as float bits)
-        reinterpret_cast<unsigned *>(a + 3)[0] = 0u;            // max F (as float bits)
+// Optional per-iteration trace of the persistent schedule (eik_set_trace):
+// records of 4 x u64 = {globaltimer ns, phase (1 Step 2, 2 Step-3 seed, 3
+// remedy), list size, tiles visited}, written by thread 0 of CTA 0 after the
+// barrier that ends each iteration.
+__device__ unsigned long long *g_trace_buf = nullptr;
+__device__ long long g_trace_cap = 0;
+
+__device__ __forceinline__ void trace_record(long long &k, unsigned long long phase, long long n, long long visited) {
+    unsigned long long *buf = g_trace_buf;
+    if (buf && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (k < g_trace_cap) {
+            unsigned long long *r = buf + 1 + 4 * k;
+            r[0] = globaltimer();
+            r[1] = phase;
+            r[2] = (unsigned long long)n;
+            r[3] = (unsigned long long)visited;
+            buf[0] = (unsigned long long)(k + 1);   // record count
+        }
+        ++k;
     }
 }
 
+// ---------------------------------------------------------------- kernels
+// Descriptor upload (by-value parameter, so that the call can be captured).
+__global__ void k_write_desc(InstDesc *desc, DescChunk chunk) {
+    const int i = threadIdx.x;
+    if (i < chunk.count) desc[chunk.first + i] = chunk.d[i];
+}
+
 // 1/delta per instance for the ordered schedule: delta = order * (mean tile
-// edge) * h / mean(F over passable nodes).
-// An instance whose passable speeds span more than kOrderContrast (e.g. slow
-// walls in a fast medium) spreads its keys over too many buckets; it is left
-// unordered (scale 0).
+// edge) * h / mean(F over passable nodes).  An instance whose passable speeds
+// span more than kOrderContrast (e.g. slow walls in a fast medium) spreads its
+// keys over too many buckets; it is left unordered (scale 0).
 constexpr double kOrderContrast = 100.0;
 
 template <int BX, int BY, int BZ>
-__global__ void k_scale(const InstDesc *desc, const double *inst_acc, float *inst_scale, int B, float order) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_scale(const InstDesc *desc, const float4 *tile_fstat, float *inst_scale, int B, float order) {
+    // one CTA per instance: reduce the per-tile statistics of its tiles
+    const int b = blockIdx.x;
     if (b >= B) return;
+    const InstDesc &d = desc[b];
+    const long long nt = (long long)d.tx * d.ty * d.tz;
+    double sum = 0.0, cnt = 0.0;
+    float mn = __int_as_float(0x7f800000), mx = 0.0f;
+    for (long long t = threadIdx.x; t < nt; t += blockDim.x) {
+        const float4 s = tile_fstat[d.tile_base + t];
+        sum += s.x; cnt += s.y; mn = fminf(mn, s.z); mx = fmaxf(mx, s.w);
+    }
+    __shared__ double s_sum[32], s_cnt[32];
+    __shared__ float s_mn[32], s_mx[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_sum[w] = sum; s_cnt[w] = cnt; s_mn[w] = mn; s_mx[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+        sum += s_sum[q]; cnt += s_cnt[q]; mn = fminf(mn, s_mn[q]); mx = fmaxf(mx, s_mx[q]);
+    }
     const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
-    const double *a = inst_acc + 4 * b;
-    const double cnt = a[1], sum = a[0];
-    const double fmn = __uint_as_float(reinterpret_cast<const unsigned *>(a + 2)[0]);
-    const double fmx = __uint_as_float(reinterpret_cast<const unsigned *>(a + 3)[0]);
     const double meanF = cnt > 0 ? sum / cnt : 0.0;
-    double sc = meanF > 0 ? meanF / ((double)order * edge * desc[b].h) : 1.0;
+    double sc = meanF > 0 ? meanF / ((double)order * edge * d.h) : 1.0;
     if (!(sc > 0) || !(sc < 1e30)) sc = 1.0;
-    if (cnt > 0 && fmx > kOrderContrast * fmn) sc = 0.0;
+    if (cnt > 0 && (double)mx > kOrderContrast * (double)mn) sc = 0.0;
     inst_scale[b] = (float)sc;
 }
 
@@ -83,24 +117,7 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_init(FwdParams<T> P) {
         P.tkey[g] = kKeyInf;
         P.tkey[P.n_tiles + g] = kKeyInf;
     }
-    if (P.ordered) {   // per-instance mean, min and max speed for the bucket width
-        float fmn = fcnt > 0 ? (float)fsum : __int_as_float(0x7f800000), fmx = fcnt > 0 ? (float)fsum : 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
-            fcnt += __shfl_xor_sync(0xffffffffu, fcnt, o);
-            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-        }
-        if ((tid & 31) == 0 && fcnt > 0) {
-            atomicAdd(P.inst_acc + 4 * s_b, fsum);
-            atomicAdd(P.inst_acc + 4 * s_b + 1, fcnt);
-            // positive floats order like their bit patterns
-            atomicMin(reinterpret_cast<unsigned *>(P.inst_acc + 4 * s_b + 2), __float_as_uint(fmn));
-            atomicMax(reinterpret_cast<unsigned *>(P.inst_acc + 4 * s_b + 3), __float_as_uint(fmx));
-        }
-    }
-    if (tid < 8) {
+    if (tid < 8) {   // tile record: neighbours, instance, key scale
         int nb;
         switch (tid) {
             case 0: nb = tx > 0 ? g - 1 : -1; break;
@@ -113,6 +130,27 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_init(FwdParams<T> P) {
             default: nb = __float_as_int(1.0f); break;   // key scale, set by k_tile_scale
         }
         P.tile_nb[8 * g + tid] = nb;
+    }
+    if (P.ordered) {   // per-tile sum, count, min and max of the passable speeds (for the bucket width)
+        __shared__ float s_red[4][32];
+        float fs = (float)fsum, fc = (float)fcnt;
+        float fmn = fcnt > 0 ? fs : __int_as_float(0x7f800000), fmx = fcnt > 0 ? fs : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fs += __shfl_xor_sync(0xffffffffu, fs, o);
+            fc += __shfl_xor_sync(0xffffffffu, fc, o);
+            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+        }
+        if ((tid & 31) == 0) { s_red[0][tid >> 5] = fs; s_red[1][tid >> 5] = fc; s_red[2][tid >> 5] = fmn; s_red[3][tid >> 5] = fmx; }
+        __syncthreads();
+        if (tid == 0) {
+            float a = 0.f, c = 0.f, mn = __int_as_float(0x7f800000), mx = 0.f;
+            for (int w = 0; w < (G::V + 31) / 32; ++w) {
+                a += s_red[0][w]; c += s_red[1][w]; mn = fminf(mn, s_red[2][w]); mx = fmaxf(mx, s_red[3][w]);
+            }
+            reinterpret_cast<float4 *>(P.tile_fstat)[g] = make_float4(a, c, mn, mx);
+        }
     }
     if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
         const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
@@ -228,6 +266,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     const int groups = gridDim.x * GroupGeom<BX, BY, BZ>::NG;
     float width = 1.0f;
     int n_prev = 0;
+    long long tk = 0;
+    trace_record(tk, 0, 0, 0);
     Ctl *ctl = P.ctl;
     unsigned long long target = 0;
     long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0, deferred = 0;
@@ -257,10 +297,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[it % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) goto done;
+        trace_record(tk, 1, n, ld_volatile(&ctl->nproc[it % 4]));
     }
     if (P.skip_remedy) goto done;
     detect_pass<T, BX, BY, BZ>(P, my, t_flag);
     if (!grid_sync(ctl, target)) goto done;
+    trace_record(tk, 2, P.n_tiles, ld_volatile(&ctl->rcnt[0]));
     // the Step-2 counters are idle from here on: nproc slots restart for Step 3
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) ctl->nproc[q] = 0;
@@ -292,6 +334,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) goto done;
+        trace_record(tk, 3, n, ld_volatile(&ctl->nproc[r % 4]));
     }
 done:
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -33,7 +33,8 @@ def test_every_declared_symbol_is_exported():
     lib = _lib.load()
     names = _declared_functions()
     assert {"eik_solve", "eik_solve_batched", "eik_workspace_size", "eik_last_error", "eik_adjoint",
-            "eik_adjoint_batched", "eik_adjoint_workspace_size_batched", "eik_solve_noalloc"} <= names
+            "eik_adjoint_batched", "eik_adjoint_workspace_size_batched", "eik_solve_noalloc",
+            "eik_set_trace"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 

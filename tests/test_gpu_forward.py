@@ -296,3 +296,17 @@ def test_converge_sweep_rule(schedule, order):
     inst = W.oscillating_3d(44)
     got, st = gpu_solve(inst, "fp32", schedule=schedule, order=order, converge="sweep", tile="8x4x4")
     assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
+def test_trace_records_iterations():
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    inst = W.oscillating_3d(40)
+    F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
+    with api.Trace() as tr:
+        phi, st = api.solve(F, inst.src_idx, inst.h, schedule="persistent", return_stats=True)
+    s = tr.summary()
+    assert s["update"]["iterations"] == st["iters_update"]
+    assert s.get("remedy", {}).get("iterations", 0) == st["iters_remedy"]
+    assert s["update"]["visited"] == st["tiles_update"]
+    assert np.all(np.diff(tr.records[:, 0]) >= 0)
