@@ -44,9 +44,12 @@ FALLBACK_HBM_GBS = 6400.0
 # k_persistent, k_unpack
 LAUNCHES_PER_SOLVE = 7
 
-# DRAM traffic of one k_persistent launch on the default workload, from an
-# ncu capture (profiles/); valid only while the kernel sources hash matches.
-MEASURED_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_persistent launch,
+# from the ncu capture summarised in profiles/k_persistent_oscillating256.md; reported only
+# while the kernel sources still hash to the captured version (else null).
+MEASURED_TRAFFIC = {
+    "oscillating_256": {"hash": "ccf4e34f36f0e199", "bytes": 374044672 + 94237952},
+}
 
 
 def kernel_source_hash() -> str:
