@@ -332,3 +332,96 @@ class Trace:
                                  median_us=float(np.median(dt[m])), mean_list=float(r[1:, 2][m].mean()),
                                  visited=int(r[1:, 3][m].sum()))
         return out
+
+
+class BatchedSolver:
+    """A fixed batch of grids and sources whose solve is captured once in a CUDA
+    graph and replayed (the batched form: all instances in one persistent
+    launch, the launch sequence replayed without host work).
+
+        bs = BatchedSolver([(F0, src0, h0), (F1, src1, h1), ...])
+        bs.set_speeds(b, F_new)      # optional: overwrite instance b's speeds in place
+        phis = bs.solve()            # replay; views into one packed output buffer
+
+    Inputs are copied once into static device buffers; set_speeds / set_sources
+    overwrite them between replays.  Every solve re-initialises all device
+    state, so replays are independent.  With graph=False the same launches are
+    issued directly (for comparison).
+    """
+
+    def __init__(self, problems, *, tile="auto", order=0.0, converge="auto", max_iters=0, graph=True):
+        F0 = problems[0][0]
+        self.device, self.dtype = F0.device, F0.dtype
+        if self.dtype not in _DT or not F0.is_cuda:
+            raise TypeError("F must be a float32/float64 CUDA tensor")
+        self.shapes, dims, idxs, vals = [], [], [], []
+        for p in problems:
+            F = p[0]
+            nx, ny, nz = _dims(F)
+            dims.append((nx, ny, nz, p[2]))
+            self.shapes.append(F.shape)
+            i = _as_index(p[1], self.device)
+            idxs.append(i)
+            vals.append(_as_values(p[3] if len(p) > 3 else None, i.numel(), self.dtype, self.device))
+        self.sizes = [d[0] * d[1] * d[2] for d in dims]
+        self.off = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
+        self.F = torch.cat([p[0].contiguous().reshape(-1).to(self.dtype) for p in problems])
+        self.phi = torch.empty_like(self.F)
+        self.nsrc = [i.numel() for i in idxs]
+        self.src_off = np.concatenate([[0], np.cumsum(self.nsrc)]).astype(np.int64)
+        self.src_idx = torch.cat(idxs) if sum(self.nsrc) else torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.src_val = torch.cat(vals) if sum(self.nsrc) else torch.zeros(1, dtype=self.dtype, device=self.device)
+        self._lib = _lib.load()
+        self._grids = _lib.grids_array(dims)
+        # the graph replays a fixed launch sequence: persistent schedule, no host reads
+        self._opt = _lib.make_options(tile, "persistent", _DT[self.dtype], False, max_iters, order, converge)
+        self._Foff, self._poff, self._soff = (_lib.i64_array(self.off), _lib.i64_array(self.off),
+                                              _lib.i64_array(self.src_off))
+        nbytes = self._lib.eik_workspace_size_batched(len(problems), self._grids, ctypes.byref(self._opt))
+        if nbytes == 0:
+            raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grids or options")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.B = len(problems)
+        self.graph = None
+        with torch.cuda.device(self.device):
+            st = _lib.eik_stats()
+            _lib.check(self._launch(ctypes.byref(st)))        # first call: checks and device set-up
+            if graph:
+                side = torch.cuda.Stream(self.device)
+                side.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(side):
+                    _lib.check(self._launch(None))            # warm the side stream
+                torch.cuda.current_stream().wait_stream(side)
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph):
+                    _lib.check(self._launch(None))
+
+    def _launch(self, stats_ptr):
+        return self._lib.eik_solve_batched(self.B, self._grids, self.F.data_ptr(), self._Foff,
+                                           self.src_idx.data_ptr(), self.src_val.data_ptr(), self._soff,
+                                           self.phi.data_ptr(), self._poff, self.ws.data_ptr(), self.ws.numel(),
+                                           _stream_ptr(), ctypes.byref(self._opt), stats_ptr)
+
+    def set_speeds(self, b: int, F: torch.Tensor):
+        self.F[self.off[b]:self.off[b] + self.sizes[b]].copy_(F.reshape(-1))
+
+    def set_sources(self, b: int, src_idx, src_val=None):
+        n = self.nsrc[b]
+        i = _as_index(src_idx, self.device)
+        if i.numel() != n:
+            raise ValueError("the number of sources of an instance is fixed by the captured graph")
+        self.src_idx[self.src_off[b]:self.src_off[b] + n].copy_(i)
+        self.src_val[self.src_off[b]:self.src_off[b] + n].copy_(_as_values(src_val, n, self.dtype, self.device))
+
+    def solve(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            _lib.check(self._launch(None))
+        return [self.phi[self.off[q]:self.off[q] + self.sizes[q]].view(self.shapes[q]) for q in range(self.B)]
+
+    def stats(self) -> dict:
+        """Run once outside the graph and return the run statistics (synchronises)."""
+        st = _lib.eik_stats()
+        _lib.check(self._launch(ctypes.byref(st)))
+        return st.as_dict()

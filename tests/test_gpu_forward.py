@@ -310,3 +310,24 @@ def test_trace_records_iterations():
     assert s.get("remedy", {}).get("iterations", 0) == st["iters_remedy"]
     assert s["update"]["visited"] == st["tiles_update"]
     assert np.all(np.diff(tr.records[:, 0]) >= 0)
+
+
+def test_batched_graph_replay_matches_and_updates():
+    """The batched solve captured in a CUDA graph: replays match the oracle, and
+    a replay after set_speeds solves the new speeds."""
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    insts = W.lognormal_batch(B=6, seed=31, lo=20, hi=44)
+    probs = [(torch.as_tensor(i.F, dtype=torch.float32).cuda(), i.src_idx, i.h) for i in insts]
+    bs = api.BatchedSolver(probs, graph=True)
+    assert bs.graph is not None
+    for _ in range(2):
+        outs = bs.solve()
+        for i, o in zip(insts, outs):
+            assert_parity(o.cpu().double().numpy(), oracle_phi(i, "fp32"), TOL32)
+    new = insts[2].F * 2.0
+    bs.set_speeds(2, torch.as_tensor(new, dtype=torch.float32).cuda())
+    outs = bs.solve()
+    ref = oracle.fmm(new.astype(np.float32).astype(np.float64), insts[2].h, insts[2].src_idx)
+    assert_parity(outs[2].cpu().double().numpy(), ref, TOL32)
+    assert_parity(outs[1].cpu().double().numpy(), oracle_phi(insts[1], "fp32"), TOL32)
