@@ -397,7 +397,11 @@ def bench_adjoint(args, dev, wsp, flush_buf):
     tb = _timed(both, flush_buf, 3)
     tp = _timed(plain, flush_buf, 2)
     n = F.numel() * len(shots)
+    _, ast = api.adjoint_batched(probs, phis, rs, shared_F=True, sum_instances=True, workspace=wsp,
+                                 return_stats=True)
     return {"workload": "tomography 192^3, 16 shots, 256 receivers", "nodes_per_pass": n,
+            "adjoint_stats": {"iterations": ast["iters_remedy"], "tile_visits": ast["tiles_remedy"],
+                              "sweeps": ast["sweeps"], "loop_ms": ast["ms_loop"]},
             "forward_ms": tf, "adjoint_ms": ta, "forward_plus_adjoint_ms": tb,
             "fwd_adj_over_fwd": tb / tf, "plain_16_solves_ms": tp, "forward_speedup_vs_plain": tp / tf,
             "forward_nodes_per_s": n / (tf / 1e3), "fwd_adj_nodes_per_s": n / (tb / 1e3)}
