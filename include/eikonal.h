@@ -174,6 +174,10 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
  *                            block (g_offsets equal) to sum their gradients
  * stats (nullable): tiles_remedy = adjoint tile visits, iters_remedy = iterations.
  * Workspace: eik_adjoint_workspace_size_batched (4 arrays of the precision per node).
+ * Options: tile and order as for the solve, but with the adjoint's own defaults
+ * (tile 8x8x8 in 3D, order 8: its lists are ordered by a static key, -max phi
+ * per tile, so lambda flows from late to early arrivals).  The result does not
+ * depend on tile, order or schedule: the sum in each node has a fixed order.
  */
 size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt);
 int eik_adjoint_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,

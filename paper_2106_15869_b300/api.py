@@ -181,7 +181,7 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
 
 
 def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances: bool = False, tile="auto",
-                    max_iters=0, return_stats=False, workspace: Workspace | None = None):
+                    max_iters=0, order=0.0, return_stats=False, workspace: Workspace | None = None):
     """Gradients dL/ds (s = 1/F) of a loss L(phi) by the adjoint of the discrete solve.
 
     problems: list of (F, src_idx, h) as for solve_batched (all on one CUDA
@@ -232,7 +232,7 @@ def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances
     src_idx = torch.cat(idxs) if sum(nsrc) else torch.zeros(0, dtype=torch.int64, device=dev)
     lib = _lib.load()
     g = _lib.grids_array(dims)
-    opt = _lib.make_options(tile, "auto", _DT[dtype], False, max_iters)
+    opt = _lib.make_options(tile, "auto", _DT[dtype], False, max_iters, order)
     B = len(problems)
     nbytes = lib.eik_adjoint_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:

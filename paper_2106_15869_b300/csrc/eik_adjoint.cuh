@@ -23,7 +23,16 @@
 // final, and the sum has a fixed order, so the result does not depend on the
 // schedule).  Neighbour tiles across faces where lambda changed are listed.
 // Sources keep lambda = 0, so they feed nothing upstream.
+//
+// Order: lambda_j is final once every neighbour with a larger phi is final,
+// so the lists are visited by a static key per tile, -max(phi) over the tile
+// in units of 1/delta (delta = order * max(phi) / (tiles along x+y+z)):
+// tiles whose key lies within the window of the list's smallest key are
+// visited, the others deferred, as in the forward's bucketed order (the
+// result does not depend on it).
 #pragma once
+
+#include <cstddef>
 
 #include "eik_kernels.cuh"
 
@@ -47,6 +56,10 @@ struct AdjParams {
     const long long *src_idx;
     long long n_src;
     T *g_out;
+    unsigned *tkey;             // [n_tiles] static key (ordered lists)
+    float *inst_scale;          // [B] 1/delta per instance
+    int ordered;
+    float order;
 };
 
 template <int BX, int BY, int BZ>
@@ -92,6 +105,17 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_adj_init(AdjParams<T> P) {
     P.lam_t[q] = T(0);
     P.r_t[q] = r;
     if (tid == 0) P.tstamp[g] = 0;
+    // largest finite phi of the tile (key of the ordered lists), block-reduced
+    __shared__ float s_mx[32];
+    float mx = phi < Num<T>::inf() ? (float)phi : -__int_as_float(0x7f800000);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < (G::V + 31) / 32; ++w) mx = fmaxf(mx, s_mx[w]);
+        P.tile_rec[8 * g + 7] = __float_as_int(mx);
+    }
     if (tid < 8) {
         int nb;
         switch (tid) {
@@ -102,11 +126,45 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_adj_init(AdjParams<T> P) {
             case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
             case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
             case 6: nb = s_b; break;
-            default: nb = 0; break;
+            default: nb = 0; break;   // slot 7 (max phi) is written above
         }
-        P.tile_rec[8 * g + tid] = nb;
+        if (tid < 7) P.tile_rec[8 * g + tid] = nb;
     }
-    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) reinterpret_cast<unsigned *>(P.ctl)[tid] = 0u;
+    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
+        const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
+        reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+    }
+}
+
+// 1/delta per instance: delta = order * max(phi) / (tiles along x + y + z); one CTA per instance.
+template <class T>
+__global__ void k_adj_scale(AdjParams<T> P) {
+    const int b = blockIdx.x;
+    if (b >= P.B) return;
+    const InstDesc &d = P.desc[b];
+    const long long nt = (long long)d.tx * d.ty * d.tz;
+    float mx = 0.0f;
+    for (long long t = threadIdx.x; t < nt; t += blockDim.x)
+        mx = fmaxf(mx, __int_as_float(P.tile_rec[8 * (d.tile_base + t) + 7]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ float s_mx[32];
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, s_mx[w]);
+    const float hops = (float)(d.tx + d.ty + d.tz);
+    P.inst_scale[b] = (mx > 0.0f && mx < __int_as_float(0x7f800000)) ? hops / (P.order * mx) : 0.0f;
+}
+
+// static key of every tile: -max(phi) / delta (larger phi first)
+template <class T>
+__global__ void k_adj_keys(AdjParams<T> P) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.n_tiles; g += gridDim.x * blockDim.x) {
+        const float mx = __int_as_float(P.tile_rec[8 * g + 7]);
+        const float sc = P.inst_scale[P.tile_rec[8 * g + 6]];
+        P.tkey[g] = (mx > -__int_as_float(0x7f800000)) ? scaled_key(-mx, sc) : key_enc(0.0f);
+    }
 }
 
 // Sources: tau = -1 marker (lambda stays 0 there).
@@ -136,6 +194,7 @@ __global__ void __launch_bounds__(BX *BY *BZ) k_adj_seed(AdjParams<T> P) {
     const int want = (P.r_t[q] != T(0) && !(P.tau_t[q] < T(0))) ? 1 : 0;
     if (__syncthreads_or(want) && threadIdx.x == 0) {
         P.tstamp[g] = 1;
+        if (P.ordered) atomicMin(&P.ctl->rkmin[0], P.tkey[g]);
         const int pos = atomicAdd(&P.ctl->rcnt[0], 1);
         if (pos < P.n_tiles) P.list0[pos] = g;
         else atomicOr(&P.ctl->flags, kFlagOverflow);
@@ -260,7 +319,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
     using GG = GroupGeom<BX, BY, BZ>;
     extern __shared__ __align__(16) unsigned char adj_smem_raw[];
     AdjSmem<T, BX, BY, BZ> *sms = reinterpret_cast<AdjSmem<T, BX, BY, BZ> *>(adj_smem_raw);
-    __shared__ int s_n;
+    __shared__ int s_n, s_p, s_visits;
+    __shared__ unsigned s_k;
     __shared__ int s_tile[GG::NG];
     __shared__ int s_nb[GG::NG][6];
     __shared__ int s_fmask[GG::NG];
@@ -269,19 +329,33 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
     // faces that never get loaded stay +inf / 0 (z of 2D tiles, far corners)
     for (int q = gt; q < AdjGeom<BX, BY, BZ>::PS; q += GG::GT) sm.phi[q] = Num<T>::inf();
     for (int q = gt; q < G::S; q += GG::GT) sm.lam[q] = T(0);
+    if (threadIdx.x == 0) s_visits = 0;
     Ctl *ctl = P.ctl;
     unsigned long long target = 0;
-    long long tiles = 0, sweeps = 0;
+    long long tiles = 0, sweeps = 0, deferred = 0;
     const int groups = gridDim.x * GG::NG;
+    float width = 1.0f;
+    int n_prev = 0;
     int r = 0;
     __syncthreads();
     for (;; ++r) {
-        if (threadIdx.x == 0) s_n = ld_volatile(&ctl->rcnt[r % 3]);
+        if (threadIdx.x == 0) {
+            s_n = ld_volatile(&ctl->rcnt[r % 3]);
+            s_k = ld_volatile_u(&ctl->rkmin[r % 3]);
+            s_p = r > 0 ? ld_volatile(&ctl->nproc[(r - 1) % 4]) : 0;
+        }
         __syncthreads();
         const int n = min(s_n, P.n_tiles);
+        if (r > 0) width = adapt_window(width, s_p, n_prev, groups, groups);
+        n_prev = n;
         if (n == 0) break;
         if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); break; }
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rcnt[(r + 2) % 3] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->rcnt[(r + 2) % 3] = 0;
+            ctl->rkmin[(r + 2) % 3] = kKeyInf;
+            ctl->nproc[(r + 2) % 4] = 0;
+        }
+        const OrderCtx ord = order_begin(P.ordered, s_k, width);
         const int nslot = (r + 1) % 3;
         const int *in = (r & 1) ? P.list1 : P.list0;
         int *out = (r & 1) ? P.list0 : P.list1;
@@ -297,13 +371,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
             }
             group_sync(bid, GG::GT);
             const int g = s_tile[gi];
+            if (ord.on) {
+                const unsigned key = __ldg(P.tkey + g);
+                if (!order_visit(ord, key)) {     // deferred: listed again, not visited
+                    if (gt < 32) {
+                        bool want = false;
+                        if (gt == 0) {
+                            want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
+                            deferred++;
+                        }
+                        warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, &ctl->rkmin[nslot], key);
+                    }
+                    continue;
+                }
+            }
             int nb[6];
 #pragma unroll
             for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
             unsigned mine;
             bool changed;
             const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
-            if (gt == 0) { tiles++; sweeps += s; }
+            if (gt == 0) { tiles++; sweeps += s; atomicAdd(&s_visits, 1); }
 #pragma unroll
             for (int m = 0; m < GG::NPT; ++m)
                 if (mine >> m & 1) {
@@ -316,16 +404,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
                 int cand = -1;
                 if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
                 if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+                const unsigned kc = (ord.on && cand >= 0) ? __ldg(P.tkey + cand) : kKeyInf;
                 const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
-                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand);
+                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters_remedy = r;
     if (threadIdx.x == 0) {
         if (tiles) atomicAdd((unsigned long long *)&ctl->tiles_remedy, (unsigned long long)tiles);
         if (sweeps) atomicAdd((unsigned long long *)&ctl->sweeps, (unsigned long long)sweeps);
+        if (deferred) atomicAdd((unsigned long long *)&ctl->tiles_deferred, (unsigned long long)deferred);
     }
 }
 

@@ -39,8 +39,8 @@ def test_adjoint_fp64_matches_oracle(seed):
     rng = np.random.default_rng(seed)
     r = np.where(np.isfinite(phi) & (rng.random(phi.shape) < 0.3), rng.standard_normal(phi.shape), 0.0)
     want = oracle.adjoint(inst.F, inst.h, inst.src_idx, phi, r)
-    for tile in ("8x8x4", "4x4x4", "8x8x8"):
-        got = gpu_adjoint(inst.F, inst.h, inst.src_idx, phi, r, "fp64", tile=tile)
+    for tile, order in (("8x8x4", 0.0), ("4x4x4", 0.0), ("8x8x8", 0.0), ("8x8x4", -1.0), ("4x4x4", 1.0)):
+        got = gpu_adjoint(inst.F, inst.h, inst.src_idx, phi, r, "fp64", tile=tile, order=order)
         scale = max(np.max(np.abs(want)), 1e-300)
         assert np.max(np.abs(got - want)) <= 1e-10 * scale, tile
 
