@@ -91,7 +91,7 @@ typedef struct {
 
 /* per-call options; a zero-filled struct (or NULL) selects the defaults */
 typedef struct {
-    int32_t tile;         /* EIK_TILE_* (0 = auto: 16x16x1 for 2D, else 8x8x4) */
+    int32_t tile;         /* EIK_TILE_* (0 = auto: 16x16x1 for 2D, else 8x8x8) */
     int32_t schedule;     /* EIK_SCHED_* (0 = auto: persistent when co-residency allows) */
     int64_t max_iters;    /* cap per loop (update, remedy); 0 = automatic */
     int32_t precision;    /* EIK_FP32 / EIK_FP64 */

@@ -90,7 +90,7 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
     if (out.tile < 0 || out.tile > EIK_TILE_8x8x1) return false;
     bool all2d = true;
     for (int64_t b = 0; b < B; ++b) all2d = all2d && grids[b].nz == 1;
-    if (out.tile == EIK_TILE_AUTO) out.tile = all2d ? EIK_TILE_16x16x1 : EIK_TILE_8x8x4;
+    if (out.tile == EIK_TILE_AUTO) out.tile = all2d ? EIK_TILE_16x16x1 : EIK_TILE_8x8x8;
     if ((out.tile == EIK_TILE_16x16x1 || out.tile == EIK_TILE_8x8x1) && !all2d) return false;
     if (out.max_iters < 0) return false;
     return true;

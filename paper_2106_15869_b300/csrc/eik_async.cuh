@@ -229,7 +229,7 @@ __device__ void async_detect_pass(const FwdParams<T> &P, const AsyncQ &Q, T *sm,
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                low |= local_solve<T>(ax, ay, az, tau[m]) < v[m];
+                low |= sweep_solve(ax, ay, az, tau[m]) < v[m];
             }
         }
         if (__any_sync(kFull, low) && lane == 0) {

@@ -156,6 +156,35 @@ __device__ __forceinline__ T local_solve(T ax, T ay, T az, T tau) {
     return a1 + (d2 + d3 + vsqrt(disc)) * (T(1) / T(3));
 }
 
+// FP32 form for the relaxation sweeps, where the latency of one root is on the
+// critical path of the wavefront: the same cascade, but the three candidate
+// roots are formed at once (their square roots overlap) and then selected,
+// and the square root is x * rsqrt(x) (a few ulp; the FP32 solve is judged at
+// 1e-4 of max(phi)).  A candidate whose branch is not taken may be NaN or inf
+// (an infinite minimum); it is never selected.
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+__device__ __forceinline__ float local_solve_fast(float ax, float ay, float az, float tau) {
+    const float lo = fminf(ax, ay), hi = fmaxf(ax, ay);
+    const float a1 = fminf(lo, az);
+    const float a3 = fmaxf(hi, az);
+    const float a2 = fmaxf(lo, fminf(hi, az));
+    const float u1 = a1 + tau;
+    const float d2 = a2 - a1, d3 = a3 - a1, d32 = d3 - d2;
+    const float t2 = tau * tau;
+    const float u2 = a1 + 0.5f * (d2 + sqrt_approx(2.0f * t2 - d2 * d2));
+    const float u3 = a1 + (d2 + d3 + sqrt_approx(3.0f * t2 - (d2 * d2 + d3 * d3 + d32 * d32))) * (1.0f / 3.0f);
+    return u1 <= a2 ? u1 : (u2 <= a3 ? u2 : u3);
+}
+
+// the root used by the relaxation sweeps: fast form in FP32, exact form in FP64
+__device__ __forceinline__ float sweep_solve(float ax, float ay, float az, float tau) {
+    return local_solve_fast(ax, ay, az, tau);
+}
+__device__ __forceinline__ double sweep_solve(double ax, double ay, double az, double tau) {
+    return local_solve<double>(ax, ay, az, tau);
+}
+
 // Device-wide barrier for a cooperative launch.  Every wait is bounded by
 // kWaitLimitNs; on a timeout the block raises ctl->abort and every block
 // leaves at its next barrier.  Returns false when the launch must stop.

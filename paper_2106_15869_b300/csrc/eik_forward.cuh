@@ -200,7 +200,7 @@ __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NP
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = local_solve<T>(ax, ay, az, tau[m]);
+                const T u = sweep_solve(ax, ay, az, tau[m]);
                 if (u < v[m]) { v[m] = u; sm[c] = u; ch |= 1u << m; }
             }
         }
@@ -379,7 +379,7 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = local_solve<T>(ax, ay, az, tau[m]);
+                const T u = sweep_solve(ax, ay, az, tau[m]);
                 if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
             }
         }

@@ -2,9 +2,9 @@
 //
 // In an iteration with a short list (the usual case in Step 2, where the
 // Active set is a thin band) the iteration time is the latency of one tile
-// visit, not throughput.  There, a group of GT threads (GT = min(V, CTA))
-// owns a tile with one node per thread (two for 512-node tiles), so a sweep
-// costs one local solve plus a named barrier instead of V/32 solves in a row;
+// visit, not throughput.  There, a group of GT threads (GT = min(V, 128))
+// owns a tile with V/GT nodes per thread (1 to 4), so a sweep costs a few
+// local solves plus a named barrier instead of V/32 solves in a row;
 // the group's OR-barrier is the convergence flag.  The rules applied are
 // exactly those of the warp passes in eik_forward.cuh; an iteration uses one
 // mode or the other for all its tiles (every CTA sees the same list size).
@@ -14,11 +14,15 @@
 
 namespace eik {
 
+// threads per latency-mode group: at most kGroupThreads, so that a CTA holds
+// several groups and an iteration keeps more tiles in flight
+constexpr int kGroupThreads = 128;
+
 template <int BX, int BY, int BZ>
 struct GroupGeom {
     using G = TileGeom<BX, BY, BZ>;
     static constexpr int CTA = 32 * kWarpsPerCta;
-    static constexpr int GT = G::V >= CTA ? CTA : G::V;   // threads per group
+    static constexpr int GT = G::V >= kGroupThreads ? kGroupThreads : G::V;   // threads per group
     static constexpr int NG = CTA / GT;                    // groups per CTA
     static constexpr int NPT = G::V / GT;                  // nodes per thread
     static_assert(NG <= kWarpsPerCta && NG <= 8, "one staged block per group");
@@ -83,7 +87,7 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
                 const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
                 const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
                 const T az = vmin(sm[c[m] - G::SX * G::SY], sm[c[m] + G::SX * G::SY]);
-                const T u = local_solve<T>(ax, ay, az, tau[m]);
+                const T u = sweep_solve(ax, ay, az, tau[m]);
                 if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
             }
         }
@@ -99,16 +103,13 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     return s;
 }
 
-// Thread 0 of the group: tile id, key and neighbours of list entry idx.
+// Thread 0 of the group: the record (neighbours, key scale) of tile g.
 template <class T>
-__device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc, const int *in, int idx,
-                                            unsigned *kcur_or_null) {
-    const int g = __ldcg(in + idx);
+__device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc, int g, unsigned key) {
     gc.tile = g;
+    gc.key = key;
     const int4 r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g));
     const int4 r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4));
-    gc.key = kcur_or_null ? __ldcg(kcur_or_null + g) : kKeyInf;
-    if (kcur_or_null) __stcg(kcur_or_null + g, kKeyInf);   // no one writes this parity in this iteration
     gc.nb[0] = r0.x; gc.nb[1] = r0.y; gc.nb[2] = r0.z; gc.nb[3] = r0.w; gc.nb[4] = r1.x; gc.nb[5] = r1.y;
     gc.scale = __int_as_float(r1.w);
     gc.fmask = 0;
@@ -120,11 +121,23 @@ __device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc,
 template <int BX, int BY, int BZ>
 __device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>::faces_of(q); }
 
-// Step 2, latency mode.
-template <class T, int BX, int BY, int BZ>
-__device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, int it, int n, unsigned kmin_cur,
-                                  float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
-                                  long long &st_def) {
+// Per-CTA queue of the tiles to visit in this iteration (latency mode).
+constexpr int kVisitQueue = 256;
+struct VisitQueue {
+    int tile[kVisitQueue];
+    unsigned key[kVisitQueue];
+    int n;
+};
+
+// Latency-mode iteration over a list: every CTA takes a contiguous chunk of
+// the list; all its threads classify the entries at once (a deferred entry is
+// listed again on the spot) and queue the tiles to visit in shared memory;
+// then the CTA's thread groups visit the queued tiles.  Chunks longer than the
+// queue are taken in pieces.  `remedy` selects the Step-3 rules (stamps).
+template <class T, int BX, int BY, int BZ, bool remedy>
+__device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int it, int n,
+                           unsigned kmin_cur, float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
+                           long long &st_def) {
     using G = TileGeom<BX, BY, BZ>;
     using GG = GroupGeom<BX, BY, BZ>;
     Ctl *ctl = P.ctl;
@@ -133,133 +146,135 @@ __device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gc
     int *out = (it & 1) ? P.list0 : P.list1;
     unsigned *kcur = P.tkey + (size_t)(it & 1) * P.n_tiles;
     unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
-    const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
+    int *cnt_next = remedy ? &ctl->rcnt[nslot] : &ctl->cnt[nslot];
+    unsigned *kmin_next = remedy ? &ctl->rkmin[nslot] : &ctl->kmin[nslot];
+    const int next_stamp = it + 2;
+    const int tid = threadIdx.x;
+    const int gi = tid / GG::GT, gt = tid % GG::GT, bid = 1 + gi;
     T *sm = smbase + (size_t)gi * G::S;
     GroupCtl &gc = gcs[gi];
     const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
-    const int groups = gridDim.x * GG::NG;
-    for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
-        group_sync(bid, GG::GT);                       // previous visit fully done with gc
-        if (gt == 0) group_fetch(P, gc, in, idx, ord.on ? kcur : nullptr);
-        group_sync(bid, GG::GT);
-        const int g = gc.tile;
-        const unsigned key = gc.key;
-        if (ord.on && !order_visit(ord, key)) {       // deferred: listed again, not visited
-            if (gt < 32) {
-                if (gt == 0) { atomicMin(knext + g, key); st_def++; }
-                warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, gt == 0, g, &ctl->kmin[nslot], key);
+    const long long c0 = (long long)n * blockIdx.x / gridDim.x, c1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
+    for (long long base = c0; base < c1; base += kVisitQueue) {
+        const long long pe = min(base + (long long)kVisitQueue, c1);
+        if (tid == 0) q.n = 0;
+        __syncthreads();
+        // classify (uniform trip count over the CTA, so the warp pushes see every lane)
+        for (long long e0 = base; e0 < pe; e0 += blockDim.x) {
+            const long long e = e0 + tid;
+            const bool valid = e < pe;
+            const int g = valid ? __ldcg(in + e) : -1;
+            unsigned key = kKeyInf;
+            if (valid && ord.on) {
+                key = __ldcg(kcur + g);
+                __stcg(kcur + g, kKeyInf);               // no one writes this parity in this iteration
             }
-            continue;
+            const bool defer = valid && ord.on && !order_visit(ord, key);
+            bool want = false;
+            if (defer) {
+                atomicMin(knext + g, key);
+                want = remedy ? atomicExch(P.tstamp + g, next_stamp) != next_stamp : true;
+                st_def++;
+            }
+            warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
+            if (valid && !defer) {
+                const int pos = atomicAdd(&q.n, 1);
+                q.tile[pos] = g;
+                q.key[pos] = key;
+            }
         }
-        T v[GG::NPT];
-        unsigned mine;
-        bool changed;
-        const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
-        if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
-        if (changed && (!P.one_visit || s >= P.max_sweeps)) {
-            if (gt < 32) {
-                if (ord.on && gt == 0) atomicMin(knext + g, key);
-                warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, gt == 0, g, ord.on ? &ctl->kmin[nslot] : nullptr, key);
-            }
-            continue;
-        }
-        // converged: Active -> Source, Distant face neighbours become Active
-        if (ord.on) {
-#pragma unroll
-            for (int m = 0; m < GG::NPT; ++m) {
-                const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
-                for (int f = 0; f < 6; ++f)
-                    if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-            }
+        __syncthreads();
+        const int qn = q.n;
+        // visit
+        for (int qi = gi; qi < qn; qi += GG::NG) {
+            group_sync(bid, GG::GT);                   // previous visit fully done with gc
+            if (gt == 0) group_fetch(P, gc, q.tile[qi], q.key[qi]);
             group_sync(bid, GG::GT);
-        }
-        if (gt < 32) {
-            if (gt == 0) __stcg(P.tstate + g, (int)kSource);
-            const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
-            const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
-            const bool act = prev == (int)kDistant;
-            unsigned kf = kKeyInf;
-            if (ord.on && nbf >= 0) {
-                kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
-                if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+            const int g = gc.tile;
+            const unsigned key = gc.key;
+            T v[GG::NPT];
+            unsigned mine;
+            bool changed;
+            const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
+            if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
+            if (!remedy) {
+                if (changed && (!P.one_visit || s >= P.max_sweeps)) {
+                    // stays Active; its next visit confirms (or not) that it converged
+                    if (gt < 32) {
+                        if (ord.on && gt == 0) atomicMin(knext + g, key);
+                        warp_push(ctl, cnt_next, out, P.n_tiles, gt == 0, g, ord.on ? kmin_next : nullptr, key);
+                    }
+                    continue;
+                }
+                // converged: Active -> Source, Distant face neighbours become Active
+                if (ord.on) {
+#pragma unroll
+                    for (int m = 0; m < GG::NPT; ++m) {
+                        const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                        for (int f = 0; f < 6; ++f)
+                            if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+                    }
+                    group_sync(bid, GG::GT);
+                }
+                if (gt < 32) {
+                    if (gt == 0) __stcg(P.tstate + g, (int)kSource);
+                    const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
+                    const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
+                    const bool act = prev == (int)kDistant;
+                    unsigned kf = kKeyInf;
+                    if (ord.on && nbf >= 0) {
+                        kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                        if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+                    }
+                    warp_push(ctl, cnt_next, out, P.n_tiles, act, nbf, ord.on ? kmin_next : nullptr, kf);
+                }
+            } else {
+                // faces where a node dropped, and (ordered) the smallest dropped value on each
+#pragma unroll
+                for (int m = 0; m < GG::NPT; ++m) {
+                    if (!(mine >> m & 1)) continue;
+                    const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                    if (fb) {
+                        atomicOr(&gc.fmask, fb);
+                        if (ord.on)
+                            for (int f = 0; f < 6; ++f)
+                                if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+                    }
+                }
+                group_sync(bid, GG::GT);
+                if (gt < 32) {
+                    const int fm = gc.fmask;
+                    int cand = -1;
+                    if (gt < 6 && (fm >> gt & 1) && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles) cand = gc.nb[gt];
+                    if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+                    unsigned kc = kKeyInf;
+                    if (ord.on && cand >= 0) {
+                        kc = gt == 6 ? key : scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                        atomicMin(knext + cand, kc);
+                    }
+                    const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+                    if (ord.on && cand >= 0 && !want) atomicMin(kmin_next, kc);
+                    warp_push(ctl, cnt_next, out, P.n_tiles, want, cand, ord.on ? kmin_next : nullptr, kc);
+                }
             }
-            warp_push(ctl, &ctl->cnt[nslot], out, P.n_tiles, act, nbf, ord.on ? &ctl->kmin[nslot] : nullptr, kf);
         }
+        __syncthreads();                               // the queue is reused by the next piece
     }
 }
 
-// Step 3b, latency mode.
 template <class T, int BX, int BY, int BZ>
-__device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, int r, int n, unsigned kmin_cur,
-                                  float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
-                                  long long &st_def) {
-    using G = TileGeom<BX, BY, BZ>;
-    using GG = GroupGeom<BX, BY, BZ>;
-    Ctl *ctl = P.ctl;
-    const int nslot = (r + 1) % 3;
-    const int *in = (r & 1) ? P.list1 : P.list0;
-    int *out = (r & 1) ? P.list0 : P.list1;
-    unsigned *kcur = P.tkey + (size_t)(r & 1) * P.n_tiles;
-    unsigned *knext = P.tkey + (size_t)((r + 1) & 1) * P.n_tiles;
-    const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
-    T *sm = smbase + (size_t)gi * G::S;
-    GroupCtl &gc = gcs[gi];
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
-    n = min(n, P.n_tiles);
-    const int next_stamp = r + 2;
-    const int groups = gridDim.x * GG::NG;
-    for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
-        group_sync(bid, GG::GT);
-        if (gt == 0) group_fetch(P, gc, in, idx, ord.on ? kcur : nullptr);
-        group_sync(bid, GG::GT);
-        const int g = gc.tile;
-        const unsigned key = gc.key;
-        if (ord.on && !order_visit(ord, key)) {
-            if (gt < 32) {
-                bool want = false;
-                if (gt == 0) {
-                    atomicMin(knext + g, key);
-                    want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
-                    st_def++;
-                }
-                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, &ctl->rkmin[nslot], key);
-            }
-            continue;
-        }
-        T v[GG::NPT];
-        unsigned mine;
-        bool changed;
-        const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
-        if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
-        // faces where a node dropped, and (ordered) the smallest dropped value on each
-#pragma unroll
-        for (int m = 0; m < GG::NPT; ++m) {
-            if (!(mine >> m & 1)) continue;
-            const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
-            if (fb) {
-                atomicOr(&gc.fmask, fb);
-                if (ord.on)
-                    for (int f = 0; f < 6; ++f)
-                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-            }
-        }
-        group_sync(bid, GG::GT);
-        if (gt < 32) {
-            const int fm = gc.fmask;
-            int cand = -1;
-            if (gt < 6 && (fm >> gt & 1) && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles) cand = gc.nb[gt];
-            if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
-            unsigned kc = kKeyInf;
-            if (ord.on && cand >= 0) {
-                kc = gt == 6 ? key : scaled_key(key_dec(gc.fmin[gt]), gc.scale);
-                atomicMin(knext + cand, kc);
-            }
-            const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
-            if (ord.on && cand >= 0 && !want) atomicMin(&ctl->rkmin[nslot], kc);
-            warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
-        }
-    }
+__device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int it, int n,
+                                  unsigned kmin_cur, float width, int *s_visits, long long &st_tiles,
+                                  long long &st_sweeps, long long &st_def) {
+    group_pass<T, BX, BY, BZ, false>(P, smbase, gcs, q, it, n, kmin_cur, width, s_visits, st_tiles, st_sweeps, st_def);
+}
+
+template <class T, int BX, int BY, int BZ>
+__device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int r, int n,
+                                  unsigned kmin_cur, float width, int *s_visits, long long &st_tiles,
+                                  long long &st_sweeps, long long &st_def) {
+    group_pass<T, BX, BY, BZ, true>(P, smbase, gcs, q, r, n, kmin_cur, width, s_visits, st_tiles, st_sweeps, st_def);
 }
 
 }  // namespace eik

@@ -13,8 +13,9 @@
 
 namespace eik {
 
-// latency mode when the list holds at most this many tiles per thread group
-constexpr int kGroupModeFactor = 2;
+// latency mode when the list holds at most this many entries per thread group
+// (deferred entries are classified by all threads of a CTA, so they are cheap)
+constexpr int kGroupModeFactor = 8;
 
 // Optional per-iteration trace of the persistent schedule (eik_set_trace):
 // records of 4 x u64 = {globaltimer ns, phase (1 Step 2, 2 Step-3 seed, 3
@@ -225,15 +226,22 @@ __global__ void k_sources(FwdParams<T> P) {
     }
 }
 
+// Statistics of one thread, summed over its warp, added to the control block.
 template <class T>
 __device__ __forceinline__ void flush_stats(const FwdParams<T> &P, long long a, long long b, long long c,
                                             long long d, long long e) {
+    unsigned long long v[5] = {(unsigned long long)a, (unsigned long long)b, (unsigned long long)c,
+                               (unsigned long long)d, (unsigned long long)e};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     if (lane_id() == 0) {
-        if (e) atomicAdd((unsigned long long *)&P.ctl->tiles_deferred, (unsigned long long)e);
-        if (a) atomicAdd((unsigned long long *)&P.ctl->tiles_update, (unsigned long long)a);
-        if (b) atomicAdd((unsigned long long *)&P.ctl->tiles_flagged, (unsigned long long)b);
-        if (c) atomicAdd((unsigned long long *)&P.ctl->tiles_remedy, (unsigned long long)c);
-        if (d) atomicAdd((unsigned long long *)&P.ctl->sweeps, (unsigned long long)d);
+        if (v[4]) atomicAdd((unsigned long long *)&P.ctl->tiles_deferred, v[4]);
+        if (v[0]) atomicAdd((unsigned long long *)&P.ctl->tiles_update, v[0]);
+        if (v[1]) atomicAdd((unsigned long long *)&P.ctl->tiles_flagged, v[1]);
+        if (v[2]) atomicAdd((unsigned long long *)&P.ctl->tiles_remedy, v[2]);
+        if (v[3]) atomicAdd((unsigned long long *)&P.ctl->sweeps, v[3]);
     }
 }
 
@@ -258,6 +266,7 @@ template <class T, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_persistent(FwdParams<T> P) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ VisitQueue vq;
     __shared__ int s_n, s_p, s_visits;
     __shared__ unsigned s_k;
     T *my = sm.phi[warp_in_cta()];
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
             ctl->nproc[(it + 2) % 4] = 0;
         }
         if (n <= kGroupModeFactor * groups)
-            update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
+            update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
         else
             update_pass<T, BX, BY, BZ>(P, my, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
         __syncthreads();
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
             ctl->nproc[(r + 2) % 4] = 0;
         }
         if (n <= kGroupModeFactor * groups)
-            remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
+            remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
         else
             remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
         __syncthreads();
@@ -364,6 +373,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                                                                               int prev_n) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ VisitQueue vq;
     __shared__ int s_visits;
     const int n = ld_volatile(&P.ctl->cnt[it % 3]);
     const unsigned kq = ld_volatile_u(&P.ctl->kmin[it % 3]);
@@ -378,7 +388,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     }
     __syncthreads();
     if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
-        update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t, s, d);
+        update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, it, n, kq, width, &s_visits, t, s, d);
     else
         update_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], it, n, kq, width, &s_visits, t, s, d);
     __syncthreads();
@@ -400,6 +410,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                                                                               int prev_n) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ VisitQueue vq;
     __shared__ int s_visits;
     const int n = ld_volatile(&P.ctl->rcnt[r % 3]);
     const unsigned kq = ld_volatile_u(&P.ctl->rkmin[r % 3]);
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     }
     __syncthreads();
     if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
-        remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t, s, d);
+        remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, r, n, kq, width, &s_visits, t, s, d);
     else
         remedy_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], r, n, kq, width, &s_visits, t, s, d);
     __syncthreads();
