@@ -79,6 +79,19 @@ extern "C" {
 #define EIK_CONVERGE_CONFIRM 1
 #define EIK_CONVERGE_SWEEP 2
 
+/* method (the loop structure; both reach the same discrete solution):
+ *   IFIM  Algorithm 2 (Sec. 3): Step 2 without neighbour convergence checks,
+ *         then the remedy pass (Step 3)
+ *   FIM   the fast iterative method of Sec. 2.3 at tile granularity: a
+ *         visit relaxes the tile to its local fixed point, and every
+ *         neighbour tile across a face whose values dropped is listed again,
+ *         whatever its state (the neighbour convergence check, taken by the
+ *         neighbour's own next visit); no Step 3.  `converge` and
+ *         `skip_remedy` do not apply, and its one loop is reported in the
+ *         Step-3 statistics (iters_remedy, tiles_remedy) */
+#define EIK_METHOD_IFIM 0
+#define EIK_METHOD_FIM 1
+
 /* precision */
 #define EIK_FP32 0
 #define EIK_FP64 1
@@ -100,7 +113,8 @@ typedef struct {
                              tile-crossing times, < 0 = unordered (every listed tile visited in
                              every iteration, the schedule of Algorithm 2 as printed) */
     int32_t converge;     /* Step-2 convergence test of a tile (EIK_CONVERGE_*) */
-    int32_t reserved[2];  /* must be 0 */
+    int32_t method;       /* EIK_METHOD_* (0 = IFIM) */
+    int32_t reserved;     /* must be 0 */
 } eik_options;
 
 /* run statistics (filled when a stats pointer is passed; the call then synchronises) */
@@ -176,8 +190,9 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
  * Workspace: eik_adjoint_workspace_size_batched (4 arrays of the precision per node).
  * Options: tile and order as for the solve, but with the adjoint's own defaults
  * (tile 8x8x8 in 3D, order 8: its lists are ordered by a static key, -max phi
- * per tile, so lambda flows from late to early arrivals).  The result does not
- * depend on tile, order or schedule: the sum in each node has a fixed order.
+ * per tile, so lambda flows from late to early arrivals); method, converge and
+ * skip_remedy do not apply.  The result does not depend on tile, order or
+ * schedule: the sum in each node has a fixed order.
  */
 size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt);
 int eik_adjoint_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,

@@ -15,6 +15,7 @@ Functions (each cites the passage it follows in its docstring):
   fmm          fast marching (Sec. 2.1): the discrete solution
   gs           Gauss-Seidel sweeping (Sec. 2.2) to an exact fixed point
   ifim         Algorithm 2 (Steps 1-3) point by point
+  fim          the fast iterative method of Sec. 2.3 point by point
   residual     relative residual of eq. (6)
   adjoint      d(loss)/d(slowness) by back substitution on the upwind
                linearisation of eq. (6) (adjoint-state method; not in the paper)
@@ -63,6 +64,8 @@ def _load():
         lib.eko_ifim.restype = ctypes.c_int
         lib.eko_ifim.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd,
                                  ctypes.c_int, _i64, _pi64]
+        lib.eko_fim.restype = ctypes.c_int
+        lib.eko_fim.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd, _i64, _pi64]
         lib.eko_residual.restype = _d
         lib.eko_residual.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd]
         lib.eko_adjoint.restype = ctypes.c_int
@@ -162,6 +165,25 @@ def ifim(F, h: float, src_idx, src_val=None, skip_remedy: bool = False,
         raise RuntimeError("oracle ifim: max_iters reached")
     return phi, dict(update_iters=int(st[0]), remedy_iters=int(st[1]),
                      remedy_seed=int(st[2]), remedy_updates=int(st[3]))
+
+
+def fim(F, h: float, src_idx, src_val=None, max_iters: int = 10**9):
+    """The fast iterative method of Sec. 2.3 (neighbour convergence check), point by point.
+
+    Returns (phi, stats) with stats = dict(iters, listed_by_check).
+    """
+    F = _f64(F)
+    nx, ny, nz = _dims(F)
+    idx, val = _src(src_idx, src_val)
+    phi = np.empty(F.shape, dtype=np.float64)
+    st = np.zeros(2, dtype=np.int64)
+    rc = _load().eko_fim(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(val),
+                         _p(phi), int(max_iters), _p(st, _pi64))
+    if rc == -1:
+        raise ValueError("oracle fim: invalid arguments")
+    if rc == -2:
+        raise RuntimeError("oracle fim: max_iters reached")
+    return phi, dict(iters=int(st[0]), listed_by_check=int(st[1]))
 
 
 def residual(F, h: float, src_idx, phi, per_node: bool = False):

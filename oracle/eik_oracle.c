@@ -28,6 +28,9 @@
  *                    to an exact fixed point; tiny grids only
  *   eko_ifim         Algorithm 2 (Steps 1-3) point by point, with the
  *                    two-phase parallel semantics of Sec. 3.2.1
+ *   eko_fim          the fast iterative method of Sec. 2.3 (with the
+ *                    neighbour convergence check), point by point, same
+ *                    two-phase semantics
  *   eko_residual     max relative residual of eq. (6) over non-source nodes
  *   eko_adjoint      transposed upwind-linearised system solved by back
  *                    substitution in increasing-phi order (adjoint-state
@@ -410,6 +413,85 @@ int eko_ifim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
             int64_t *t = list; list = next; next = t;
             n = m;
         }
+    }
+done:
+    if (stats) memcpy(stats, st, sizeof(st));
+    free(is_fixed); free(lab); free(list); free(next); free(cand);
+    return rc;
+}
+
+/*
+ * The fast iterative method of Sec. 2.3, point by point.  Active starts as
+ * the points adjacent to the sources (as Step 1 of Algorithm 2).  Every
+ * iteration has two phases:
+ *   (a) every Active point computes phi~ from the values at the start of the
+ *       iteration;
+ *   (b) a point with phi~ == phi has converged: it leaves Active and each of
+ *       its neighbours that is neither a fixed source nor Active (now or for
+ *       the next iteration) is checked: its phi~ is computed from the current
+ *       values and, if it is below its value (the neighbour is +inf or not
+ *       converged), the neighbour takes phi~ and joins Active.  A point with
+ *       phi~ != phi takes min(phi, phi~) and stays Active.
+ * The loop ends when Active is empty.  stats (nullable, 2 entries):
+ * iterations, neighbour checks that listed a point.
+ * Returns 0, -1 on an argument error, -2 on reaching max_iters.
+ */
+int eko_fim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
+            int64_t n_src, const int64_t *src_idx, const double *src_val,
+            double *phi, int64_t max_iters, int64_t *stats) {
+    dims_t d = {nx, ny, nz};
+    if (check_args(&d, h, F, n_src, src_idx, src_val)) return -1;
+    int64_t N = nx * ny * nz;
+    unsigned char *is_fixed = malloc((size_t)N);
+    /* bit0 Active (current iteration), bit2 Active (next iteration) */
+    unsigned char *lab = calloc((size_t)N, 1);
+    int64_t *list = malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *next = malloc(sizeof(int64_t) * (size_t)N);
+    double *cand = malloc(sizeof(double) * (size_t)N);
+    int64_t st[2] = {0, 0};
+    int rc = 0;
+    init_sources(N, phi, is_fixed, n_src, src_idx, src_val);
+
+    int64_t n = 0;
+    for (int64_t p = 0; p < N; ++p) {
+        if (!is_fixed[p]) continue;
+        int64_t nb[6];
+        int nn = neighbours(&d, p, nb);
+        for (int q = 0; q < nn; ++q)
+            if (!is_fixed[nb[q]] && !(lab[nb[q]] & 1)) { lab[nb[q]] |= 1; list[n++] = nb[q]; }
+    }
+    while (n > 0) {
+        if (st[0] >= max_iters) { rc = -2; goto done; }
+        st[0]++;
+        for (int64_t a = 0; a < n; ++a)
+            cand[a] = solve_at(&d, phi, list[a], tau_of(h, F[list[a]]));
+        int64_t m = 0;
+        for (int64_t a = 0; a < n; ++a) {
+            int64_t p = list[a];
+            if (cand[a] == phi[p]) {
+                int64_t nb[6];
+                int nn = neighbours(&d, p, nb);
+                for (int q = 0; q < nn; ++q) {
+                    int64_t r = nb[q];
+                    if (is_fixed[r] || (lab[r] & 5)) continue;
+                    double u = solve_at(&d, phi, r, tau_of(h, F[r]));
+                    if (u < phi[r]) {
+                        phi[r] = u;
+                        lab[r] |= 4;
+                        next[m++] = r;
+                        st[1]++;
+                    }
+                }
+            } else {
+                if (cand[a] < phi[p]) phi[p] = cand[a];
+                lab[p] |= 4;
+                next[m++] = p;
+            }
+        }
+        for (int64_t a = 0; a < n; ++a) lab[list[a]] &= (unsigned char)~1;
+        for (int64_t a = 0; a < m; ++a) lab[next[a]] = (unsigned char)((lab[next[a]] & ~4) | 1);
+        int64_t *t = list; list = next; next = t;
+        n = m;
     }
 done:
     if (stats) memcpy(stats, st, sizeof(st));

@@ -21,6 +21,7 @@ TILES = {"auto": 0, "8x8x8": 1, "4x4x4": 2, "8x8x4": 3, "16x16x1": 4, "8x4x4": 5
 SCHEDULES = {"auto": 0, "persistent": 1, "hostloop": 2, "async": 3}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 CONVERGE = {"auto": 0, "confirm": 1, "sweep": 2}
+METHODS = {"ifim": 0, "fim": 1}
 
 
 class eik_grid(ctypes.Structure):
@@ -32,7 +33,7 @@ class eik_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("skip_remedy", ctypes.c_int32), ("order", ctypes.c_float),
-                ("converge", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("converge", ctypes.c_int32), ("method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class eik_stats(ctypes.Structure):
@@ -120,7 +121,7 @@ def check(rc: int):
 
 
 def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=False,
-                 max_iters=0, order=0.0, converge="auto") -> eik_options:
+                 max_iters=0, order=0.0, converge="auto", method="ifim") -> eik_options:
     o = eik_options()
     o.tile = TILES[tile] if isinstance(tile, str) else int(tile)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -129,6 +130,7 @@ def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=Fal
     o.max_iters = int(max_iters)
     o.order = float(order)
     o.converge = CONVERGE[converge] if isinstance(converge, str) else int(converge)
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
     return o
 
 

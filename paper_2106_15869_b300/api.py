@@ -75,7 +75,7 @@ def _workspace(device, nbytes, ws: Workspace | None):
 
 
 def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", schedule="auto",
-          skip_remedy=False, max_iters=0, order=0.0, converge="auto", return_stats=False,
+          skip_remedy=False, max_iters=0, order=0.0, converge="auto", method="ifim", return_stats=False,
           workspace: Workspace | None = None, out: torch.Tensor | None = None):
     """Arrival times phi of ||grad phi|| = 1/F with fixed values at the sources.
 
@@ -86,6 +86,10 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     (this synchronises the stream).  order: 0 = default bucketed list order,
     > 0 = bucket width in tile-crossing times, < 0 = unordered lists (every
     listed tile visited in every iteration, as Algorithm 2 is printed).
+    method: "ifim" (Algorithm 2: Step 2 without neighbour checks, then the
+    remedy) or "fim" (the fast iterative method of Sec. 2.3 at tile
+    granularity: neighbour tiles are re-listed when a visit lowers their
+    facing boundary; no remedy).  Both give the same discrete solution.
     """
     if F.dtype not in _DT:
         raise TypeError("F must be float32 or float64")
@@ -97,7 +101,7 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     val = _as_values(src_val, idx.numel(), Fd.dtype, dev)
     lib = _lib.load()
     g = _lib.grids_array([(nx, ny, nz, h)])
-    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge)
+    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge, method)
     nbytes = lib.eik_workspace_size(g, ctypes.byref(opt))
     if nbytes == 0:
         raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grid or options")
@@ -116,7 +120,8 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
 
 
 def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, max_iters=0, order=0.0,
-                  converge="auto", return_stats=False, workspace: Workspace | None = None, shared_F: bool = False):
+                  converge="auto", method="ifim", return_stats=False, workspace: Workspace | None = None,
+                  shared_F: bool = False):
     """Solve many independent grids in one set of launches.
 
     problems: list of (F, src_idx, h) or (F, src_idx, h, src_val); all F on the
@@ -158,7 +163,7 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
     src_val = torch.cat(vals) if sum(nsrc) else torch.zeros(0, dtype=dtype, device=dev)
     lib = _lib.load()
     g = _lib.grids_array(dims)
-    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge)
+    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge, method)
     B = len(problems)
     nbytes = lib.eik_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:
@@ -325,7 +330,7 @@ class Trace:
         dt = np.diff(r[:, 0]) / 1e3
         ph = r[1:, 1]
         out = {}
-        for p, name in ((1, "update"), (2, "seed"), (3, "remedy")):
+        for p, name in ((1, "update"), (2, "seed"), (3, "remedy"), (4, "fim")):
             m = ph == p
             if m.any():
                 out[name] = dict(iterations=int(m.sum()), total_us=float(dt[m].sum()),
@@ -349,7 +354,8 @@ class BatchedSolver:
     issued directly (for comparison).
     """
 
-    def __init__(self, problems, *, tile="auto", order=0.0, converge="auto", max_iters=0, graph=True):
+    def __init__(self, problems, *, tile="auto", order=0.0, converge="auto", method="ifim", max_iters=0,
+                 graph=True):
         F0 = problems[0][0]
         self.device, self.dtype = F0.device, F0.dtype
         if self.dtype not in _DT or not F0.is_cuda:
@@ -374,7 +380,7 @@ class BatchedSolver:
         self._lib = _lib.load()
         self._grids = _lib.grids_array(dims)
         # the graph replays a fixed launch sequence: persistent schedule, no host reads
-        self._opt = _lib.make_options(tile, "persistent", _DT[self.dtype], False, max_iters, order, converge)
+        self._opt = _lib.make_options(tile, "persistent", _DT[self.dtype], False, max_iters, order, converge, method)
         self._Foff, self._poff, self._soff = (_lib.i64_array(self.off), _lib.i64_array(self.off),
                                               _lib.i64_array(self.src_off))
         nbytes = self._lib.eik_workspace_size_batched(len(problems), self._grids, ctypes.byref(self._opt))

@@ -61,7 +61,7 @@ TileShape tile_shape(int tile) {
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Opts {
-    int tile, schedule, precision, skip_remedy, converge;
+    int tile, schedule, precision, skip_remedy, converge, method;
     long long max_iters;
     float order;           // <= 0: unordered lists (every listed tile visited each iteration)
 };
@@ -81,10 +81,13 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
     out.converge = o ? o->converge : EIK_CONVERGE_AUTO;
     if (out.converge < 0 || out.converge > EIK_CONVERGE_SWEEP) return false;
     if (out.converge == EIK_CONVERGE_AUTO) out.converge = EIK_CONVERGE_CONFIRM;
-    if (o) {
-        for (int q = 0; q < 2; ++q)
-            if (o->reserved[q] != 0) return false;
+    out.method = o ? o->method : EIK_METHOD_IFIM;
+    if (out.method != EIK_METHOD_IFIM && out.method != EIK_METHOD_FIM) return false;
+    if (out.method == EIK_METHOD_FIM) {
+        out.converge = EIK_CONVERGE_SWEEP;                  // a visit relaxes to the tile's local fixed point
+        out.skip_remedy = 0;
     }
+    if (o && o->reserved != 0) return false;
     if (out.precision != EIK_FP32 && out.precision != EIK_FP64) return false;
     if (out.schedule < 0 || out.schedule > EIK_SCHED_ASYNC) return false;
     if (out.tile < 0 || out.tile > EIK_TILE_8x8x1) return false;
@@ -268,6 +271,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);
     P.max_iters = o.max_iters > 0 ? o.max_iters : auto_max_iters(L);
     P.skip_remedy = o.skip_remedy;
+    P.fim = o.method == EIK_METHOD_FIM ? 1 : 0;
     P.one_visit = o.converge == EIK_CONVERGE_SWEEP ? 1 : 0;
     P.max_sweeps = 4 * (BX + BY + BZ) + 8;
     P.F = static_cast<const T *>(F);
@@ -324,7 +328,8 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         if (!di.coop || per_sm_a < 1) return fail(EIK_ERR_CUDA, "the asynchronous schedule needs a cooperative launch");
         k_queue_init<<<std::min<unsigned long long>((L.q_slots + 255) / 256, 4096), 256, 0, st>>>(Q, (int)L.n_tiles);
         EIK_CUDA(cudaGetLastError(), "k_queue_init launch");
-        k_queue_seed<<<std::max(1, std::min((int)((L.n_tiles + 255) / 256), 1024)), 256, 0, st>>>(Q, P.ctl, P.list0);
+        k_queue_seed<<<std::max(1, std::min((int)((L.n_tiles + 255) / 256), 1024)), 256, 0, st>>>(
+            Q, P.ctl, P.fim ? &P.ctl->rcnt[0] : &P.ctl->cnt[0], P.list0);
         EIK_CUDA(cudaGetLastError(), "k_queue_seed launch");
         const int grid = per_sm_a * di.sms;
         void *args[] = {&P, &Q};
@@ -353,11 +358,12 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         const int grid_cap = std::max(1, per_sm * di.sms);
         Ctl *dctl = P.ctl;
         int n = 0, prev_n = 0;
-        EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+        EIK_CUDA(cudaMemcpyAsync(&n, P.fim ? &dctl->rcnt[0] : &dctl->cnt[0], sizeof(int), cudaMemcpyDeviceToHost, st),
+                 "count copy");
         EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
         long long it = 0, r = 0;
         bool capped = false;
-        while (n > 0) {
+        while (n > 0 && !P.fim) {
             if (it >= P.max_iters) { capped = true; break; }
             k_update_iter<T, BX, BY, BZ><<<std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, grid_cap), CTA, 0, st>>>(
                 P, (int)it, prev_n);
@@ -367,13 +373,18 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
             EIK_CUDA(cudaMemcpyAsync(&n, &dctl->cnt[it % 3], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
             EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
         }
-        if (!capped && !P.skip_remedy) {
-            k_detect<T, BX, BY, BZ><<<std::min((int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta), grid_cap), CTA, 0, st>>>(P);
-            EIK_CUDA(cudaGetLastError(), "k_detect launch");
-            EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
-            const int zeros[4] = {0, 0, 0, 0};
-            EIK_CUDA(cudaMemcpyAsync(&dctl->nproc[0], zeros, sizeof(zeros), cudaMemcpyHostToDevice, st), "nproc reset");
-            EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+        if (!capped && (P.fim || !P.skip_remedy)) {
+            if (!P.fim) {
+                k_detect<T, BX, BY, BZ><<<std::min((int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta), grid_cap), CTA,
+                                          0, st>>>(P);
+                EIK_CUDA(cudaGetLastError(), "k_detect launch");
+                EIK_CUDA(cudaMemcpyAsync(&n, &dctl->rcnt[0], sizeof(int), cudaMemcpyDeviceToHost, st), "count copy");
+                const int zeros[4] = {0, 0, 0, 0};
+                EIK_CUDA(cudaMemcpyAsync(&dctl->nproc[0], zeros, sizeof(zeros), cudaMemcpyHostToDevice, st),
+                         "nproc reset");
+                EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
+            }
+            // Step 3b, or the one loop of the FIM (entered with the source tiles listed)
             prev_n = 0;
             while (n > 0) {
                 if (r >= P.max_iters) { capped = true; break; }

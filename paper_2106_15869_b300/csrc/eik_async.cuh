@@ -240,7 +240,8 @@ __device__ void async_detect_pass(const FwdParams<T> &P, const AsyncQ &Q, T *sm,
     }
 }
 
-// The whole of Steps 2 and 3 in one cooperative launch: two grid barriers.
+// The whole of Steps 2 and 3 in one cooperative launch: two grid barriers
+// (under the FIM, its one loop and none).
 template <class T, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_async(FwdParams<T> P, AsyncQ Q) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     Ctl *ctl = P.ctl;
     unsigned long long target = 0;
     long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0;
+    if (P.fim) goto neighbour_check;                   // FIM: the queue holds the source tiles
     async_update_phase<T, BX, BY, BZ>(P, Q, my, t_upd, sweeps);
     if (!grid_sync(ctl, target)) goto done;
     if (ld_volatile(&ctl->q_stop) || P.skip_remedy) goto done;
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     if (!grid_sync(ctl, target)) goto done;
     async_detect_pass<T, BX, BY, BZ>(P, Q, my, t_flag);
     if (!grid_sync(ctl, target)) goto done;
+neighbour_check:
     async_remedy_phase<T, BX, BY, BZ>(P, Q, my, t_rem, sweeps);
 done:
     flush_stats<T>(P, t_upd, t_flag, t_rem, sweeps, 0);
@@ -277,10 +280,10 @@ __global__ void k_queue_init(AsyncQ Q, int n_tiles) {
     }
 }
 
-// Step 1b for the asynchronous schedule: the initial Active tiles (listed in
-// list0 by k_sources) go into the queue.
-__global__ void k_queue_seed(AsyncQ Q, Ctl *ctl, const int *list0) {
-    const int n = min(ctl->cnt[0], (int)(Q.mask + 1));
+// Step 1b for the asynchronous schedule: the initial tiles (listed in list0 by
+// k_sources, *count of them) go into the queue.
+__global__ void k_queue_seed(AsyncQ Q, Ctl *ctl, const int *count, const int *list0) {
+    const int n = min(*count, (int)(Q.mask + 1));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int g = list0[i];
         Q.qstate[g] = kQueued;

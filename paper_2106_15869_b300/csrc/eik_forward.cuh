@@ -52,6 +52,7 @@ struct FwdParams {
     Ctl *ctl;
     long long max_iters;
     int skip_remedy;
+    int fim;                     // 1 = the fast iterative method of Sec. 2.3 (one neighbour-check loop)
     int one_visit;               // Step 2: a visit whose relaxation converged moves the tile to Source
     int max_sweeps;              // cap on in-tile sweeps per visit
     const T *F;                  // packed input speeds

@@ -129,7 +129,7 @@ struct VisitQueue {
     int n;
 };
 
-// Latency-mode iteration over a list: every CTA takes a contiguous chunk of
+// Latency-mode iteration over a list: every CTA takes an interleaved share of
 // the list; all its threads classify the entries at once (a deferred entry is
 // listed again on the spot) and queue the tiles to visit in shared memory;
 // then the CTA's thread groups visit the queued tiles.  Chunks longer than the
@@ -155,16 +155,19 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Visi
     GroupCtl &gc = gcs[gi];
     const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
-    const long long c0 = (long long)n * blockIdx.x / gridDim.x, c1 = (long long)n * (blockIdx.x + 1) / gridDim.x;
-    for (long long base = c0; base < c1; base += kVisitQueue) {
-        const long long pe = min(base + (long long)kVisitQueue, c1);
+    // this CTA's entries: blockIdx.x + j * gridDim.x for j < cnt (interleaved, so that
+    // a run of adjacent entries, typically the tiles listed by one visit, and the
+    // visits they lead to are spread over the CTAs)
+    const int cnt = n > (int)blockIdx.x ? (n - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    for (int base = 0; base < cnt; base += kVisitQueue) {
+        const int pe = min(base + kVisitQueue, cnt);
         if (tid == 0) q.n = 0;
         __syncthreads();
         // classify (uniform trip count over the CTA, so the warp pushes see every lane)
-        for (long long e0 = base; e0 < pe; e0 += blockDim.x) {
-            const long long e = e0 + tid;
+        for (int e0 = base; e0 < pe; e0 += blockDim.x) {
+            const int e = e0 + tid;
             const bool valid = e < pe;
-            const int g = valid ? __ldcg(in + e) : -1;
+            const int g = valid ? __ldcg(in + blockIdx.x + (size_t)e * gridDim.x) : -1;
             unsigned key = kKeyInf;
             if (valid && ord.on) {
                 key = __ldcg(kcur + g);

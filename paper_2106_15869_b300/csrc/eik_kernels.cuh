@@ -19,7 +19,7 @@ constexpr int kGroupModeFactor = 8;
 
 // Optional per-iteration trace of the persistent schedule (eik_set_trace):
 // records of 4 x u64 = {globaltimer ns, phase (1 Step 2, 2 Step-3 seed, 3
-// remedy), list size, tiles visited}, written by thread 0 of CTA 0 after the
+// remedy, 4 FIM loop), list size, tiles visited}, written by thread 0 of CTA 0 after the
 // barrier that ends each iteration.
 __device__ unsigned long long *g_trace_buf = nullptr;
 __device__ long long g_trace_cap = 0;
@@ -213,13 +213,16 @@ __global__ void k_sources(FwdParams<T> P) {
     if (k % BZ == 0 && k > 0) cand[nc++] = g - d.tx * d.ty;
     if (k % BZ == BZ - 1 && k + 1 < d.nz) cand[nc++] = g + d.tx * d.ty;
     const unsigned key = scaled_key((float)P.src_val[s], P.inst_scale[b]);
+    // the first list of the loop that runs first: Step 2, or the one loop of the FIM
+    int *cnt0 = P.fim ? &P.ctl->rcnt[0] : &P.ctl->cnt[0];
+    unsigned *kmin0 = P.fim ? &P.ctl->rkmin[0] : &P.ctl->kmin[0];
     for (int q = 0; q < nc; ++q) {
         if (P.ordered) {
             atomicMin(P.tkey + cand[q], key);
-            atomicMin(&P.ctl->kmin[0], key);
+            atomicMin(kmin0, key);
         }
         if (atomicCAS(P.tstate + cand[q], (int)kDistant, (int)kActive) == (int)kDistant) {
-            const int pos = atomicAdd(&P.ctl->cnt[0], 1);
+            const int pos = atomicAdd(cnt0, 1);
             if (pos < P.n_tiles) P.list0[pos] = cand[q];
             else atomicOr(&P.ctl->flags, kFlagOverflow);
         }
@@ -281,6 +284,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     unsigned long long target = 0;
     long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0, deferred = 0;
     int it = 0, r = 0;
+    if (P.fim) goto neighbour_check;                   // FIM: one loop, entered with the source tiles listed
     for (;; ++it) {
         if (threadIdx.x == 0) {
             s_n = ld_volatile(&ctl->cnt[it % 3]);
@@ -316,6 +320,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) ctl->nproc[q] = 0;
     if (!grid_sync(ctl, target)) goto done;
+neighbour_check:
+    // Step 3b; under the FIM the whole solve.  A visit lists the neighbour
+    // tiles across the faces where its values dropped, whatever their state.
     width = 1.0f;
     n_prev = 0;
     for (;; ++r) {
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) goto done;
-        trace_record(tk, 3, n, ld_volatile(&ctl->nproc[r % 4]));
+        trace_record(tk, P.fim ? 4 : 3, n, ld_volatile(&ctl->nproc[r % 4]));
     }
 done:
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -87,10 +87,15 @@ def test_host_argument_errors_before_device_work():
     assert lib.eik_solve(g, 1, None, None, -1, 1, 4096, 1 << 30, None, None, None) == _lib.EIK_ERR_ARG
     bad = _lib.grids_array([(8, 0, 8, 0.1)])
     assert lib.eik_solve(bad, 1, None, None, 0, 1, 4096, 1 << 30, None, None, None) == _lib.EIK_ERR_ARG
-    # reserved option fields must be zero
+    # the reserved option field must be zero; the method must be a known one
     o2 = _lib.make_options()
-    o2.reserved[1] = 3
+    o2.reserved = 3
     assert lib.eik_solve(g, 1, None, None, 0, 1, 4096, 1 << 30, None, ctypes.byref(o2), None) == _lib.EIK_ERR_ARG
+    for m in (-1, 2):
+        o3 = _lib.make_options(method=m)
+        assert lib.eik_solve(g, 1, None, None, 0, 1, 4096, 1 << 30, None, ctypes.byref(o3), None) == _lib.EIK_ERR_ARG
+        assert lib.eik_workspace_size(g, ctypes.byref(o3)) == 0
+    assert lib.eik_workspace_size(g, ctypes.byref(_lib.make_options(method="fim"))) > 0
     # batched: decreasing source offsets
     gb = _lib.grids_array([(8, 8, 8, 0.1), (8, 8, 8, 0.1)])
     rc = lib.eik_solve_batched(2, gb, 1, _lib.i64_array([0, 0]), 1, 1, _lib.i64_array([0, 3, 2]), 1,

@@ -331,3 +331,53 @@ def test_batched_graph_replay_matches_and_updates():
     ref = oracle.fmm(new.astype(np.float32).astype(np.float64), insts[2].h, insts[2].src_idx)
     assert_parity(outs[2].cpu().double().numpy(), ref, TOL32)
     assert_parity(outs[1].cpu().double().numpy(), oracle_phi(insts[1], "fp32"), TOL32)
+
+
+# ------------------------------------------------------------------ FIM mode (Sec. 2.3)
+@pytest.mark.parametrize("schedule", ["persistent", "hostloop", "async"])
+@pytest.mark.parametrize("tile", ["8x8x8", "4x4x4", "8x8x4"])
+def test_fim_mode_matches_oracle(schedule, tile):
+    """The tile-level FIM (neighbour tiles re-listed when a visit lowers their
+    facing boundary, no remedy) reaches the same discrete solution."""
+    inst = W.maze_3d(45, seed=11, n_slabs=3, gap=10, n_src=2)
+    ref = oracle_phi(inst, "fp64")
+    got, st = gpu_solve(inst, "fp64", schedule=schedule, tile=tile, method="fim")
+    assert_parity(got, ref, TOL64)
+    assert st["iters_update"] == 0 and st["tiles_update"] == 0 and st["tiles_flagged"] == 0
+    assert st["tiles_remedy"] > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_fim_mode_random_small(seed):
+    inst = W.random_small(100 + seed, max_edge=21, p_barrier=0.08 if seed % 2 else 0.0)
+    for dt, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        got, _ = gpu_solve(inst, dt, method="fim")
+        assert_parity(got, oracle_phi(inst, dt), tol)
+
+
+@pytest.mark.parametrize("order", [0.0, -1.0])
+def test_fim_mode_2d_and_orders(order):
+    inst = W.paper_example_2d(2, n=150)
+    for dt, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        got, _ = gpu_solve(inst, dt, method="fim", order=order)
+        assert_parity(got, oracle_phi(inst, dt), tol)
+
+
+def test_fim_mode_oracle_point_fim_agrees():
+    """The point-wise FIM of the oracle and the tile-level FIM of the library
+    end at the same values (both are the discrete solution)."""
+    inst = W.oscillating_3d(33)
+    fim, _ = oracle.fim(inst.F, inst.h, inst.src_idx, inst.src_val)
+    got, _ = gpu_solve(inst, "fp64", method="fim")
+    assert_parity(got, fim, TOL64)
+
+
+def test_fim_mode_batched():
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    insts = W.lognormal_batch(B=3, seed=9, lo=20, hi=40)
+    probs = [(torch.as_tensor(i.F, dtype=torch.float64).cuda(), i.src_idx, i.h) for i in insts]
+    phis, st = api.solve_batched(probs, method="fim", return_stats=True)
+    assert st["status"] == 0
+    for inst, phi in zip(insts, phis):
+        assert_parity(phi.cpu().numpy(), oracle_phi(inst, "fp64"), TOL64)
