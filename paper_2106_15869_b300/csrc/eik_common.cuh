@@ -57,6 +57,7 @@ struct Ctl {
     unsigned kmin[3];             // Step-2 smallest key listed for iteration it (slot it % 3)
     unsigned rkmin[3];            // Step-3 smallest key listed for iteration r
     int nproc[4];                 // tiles visited (not deferred) in iteration it (slot it % 4)
+    int grab[3], rgrab[3];        // latency mode: list entries taken so far in iteration it (slot it % 3)
     float win[2];                 // bucket width of the host-loop schedule, by iteration parity
     long long iters_update, iters_remedy;
     long long tiles_update, tiles_flagged, tiles_remedy, sweeps, tiles_deferred;

@@ -121,23 +121,32 @@ __device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc,
 template <int BX, int BY, int BZ>
 __device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>::faces_of(q); }
 
-// Per-CTA queue of the tiles to visit in this iteration (latency mode).
-constexpr int kVisitQueue = 256;
-struct VisitQueue {
-    int tile[kVisitQueue];
-    unsigned key[kVisitQueue];
+// Per-group queue of the tiles a group visits from the chunk of the list it took.
+struct GroupQueue {
+    int tile[kGroupThreads];
+    unsigned key[kGroupThreads];
     int n;
+    int base;
 };
 
-// Latency-mode iteration over a list: every CTA takes an interleaved share of
-// the list; all its threads classify the entries at once (a deferred entry is
-// listed again on the spot) and queue the tiles to visit in shared memory;
-// then the CTA's thread groups visit the queued tiles.  Chunks longer than the
-// queue are taken in pieces.  `remedy` selects the Step-3 rules (stamps).
+// List entries per grab: about one visit per chunk at the previous
+// iteration's visit rate (deferred entries are cheap, visits are not), at most
+// n / (2 groups) so that every group gets work, at most one per thread.
+__device__ __forceinline__ int group_chunk(int n, int visited_prev, int listed_prev, int groups, int gt) {
+    int c = (listed_prev > 0 && visited_prev > 0) ? listed_prev / visited_prev : n;
+    c = min(c, n / (2 * groups));
+    return max(1, min(c, gt));
+}
+
+// Latency-mode iteration over a list: every thread group takes chunks of the
+// list from a shared counter (dynamic balance: visits differ in length by an
+// order of magnitude), classifies a chunk with all its threads at once (a
+// deferred entry is listed again on the spot), queues the tiles to visit and
+// visits them one by one.  `remedy` selects the Step-3 rules (stamps).
 template <class T, int BX, int BY, int BZ, bool remedy>
-__device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int it, int n,
-                           unsigned kmin_cur, float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
-                           long long &st_def) {
+__device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int it, int n,
+                           unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
+                           long long &st_sweeps, long long &st_def) {
     using G = TileGeom<BX, BY, BZ>;
     using GG = GroupGeom<BX, BY, BZ>;
     Ctl *ctl = P.ctl;
@@ -148,26 +157,29 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Visi
     unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
     int *cnt_next = remedy ? &ctl->rcnt[nslot] : &ctl->cnt[nslot];
     unsigned *kmin_next = remedy ? &ctl->rkmin[nslot] : &ctl->kmin[nslot];
+    int *grab = remedy ? &ctl->rgrab[it % 3] : &ctl->grab[it % 3];
     const int next_stamp = it + 2;
     const int tid = threadIdx.x;
     const int gi = tid / GG::GT, gt = tid % GG::GT, bid = 1 + gi;
     T *sm = smbase + (size_t)gi * G::S;
     GroupCtl &gc = gcs[gi];
+    GroupQueue &q = gqs[gi];
     const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
-    // this CTA's entries: blockIdx.x + j * gridDim.x for j < cnt (interleaved, so that
-    // a run of adjacent entries, typically the tiles listed by one visit, and the
-    // visits they lead to are spread over the CTAs)
-    const int cnt = n > (int)blockIdx.x ? (n - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    for (int base = 0; base < cnt; base += kVisitQueue) {
-        const int pe = min(base + kVisitQueue, cnt);
-        if (tid == 0) q.n = 0;
-        __syncthreads();
-        // classify (uniform trip count over the CTA, so the warp pushes see every lane)
-        for (int e0 = base; e0 < pe; e0 += blockDim.x) {
-            const int e = e0 + tid;
-            const bool valid = e < pe;
-            const int g = valid ? __ldcg(in + blockIdx.x + (size_t)e * gridDim.x) : -1;
+    chunk = max(1, min(chunk, GG::GT));
+    for (;;) {
+        if (gt == 0) {
+            q.n = 0;
+            q.base = atomicAdd(grab, chunk);
+        }
+        group_sync(bid, GG::GT);
+        const int base = q.base;
+        if (base >= n) break;                          // group-uniform
+        // classify: one entry per thread (every lane of the group's warps takes part in the pushes)
+        {
+            const int e = base + gt;
+            const bool valid = gt < chunk && e < n;
+            const int g = valid ? __ldcg(in + e) : -1;
             unsigned key = kKeyInf;
             if (valid && ord.on) {
                 key = __ldcg(kcur + g);
@@ -187,11 +199,10 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Visi
                 q.key[pos] = key;
             }
         }
-        __syncthreads();
+        group_sync(bid, GG::GT);
         const int qn = q.n;
         // visit
-        for (int qi = gi; qi < qn; qi += GG::NG) {
-            group_sync(bid, GG::GT);                   // previous visit fully done with gc
+        for (int qi = 0; qi < qn; ++qi) {
             if (gt == 0) group_fetch(P, gc, q.tile[qi], q.key[qi]);
             group_sync(bid, GG::GT);
             const int g = gc.tile;
@@ -208,29 +219,29 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Visi
                         if (ord.on && gt == 0) atomicMin(knext + g, key);
                         warp_push(ctl, cnt_next, out, P.n_tiles, gt == 0, g, ord.on ? kmin_next : nullptr, key);
                     }
-                    continue;
-                }
-                // converged: Active -> Source, Distant face neighbours become Active
-                if (ord.on) {
+                } else {
+                    // converged: Active -> Source, Distant face neighbours become Active
+                    if (ord.on) {
 #pragma unroll
-                    for (int m = 0; m < GG::NPT; ++m) {
-                        const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
-                        for (int f = 0; f < 6; ++f)
-                            if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+                        for (int m = 0; m < GG::NPT; ++m) {
+                            const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                            for (int f = 0; f < 6; ++f)
+                                if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+                        }
+                        group_sync(bid, GG::GT);
                     }
-                    group_sync(bid, GG::GT);
-                }
-                if (gt < 32) {
-                    if (gt == 0) __stcg(P.tstate + g, (int)kSource);
-                    const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
-                    const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
-                    const bool act = prev == (int)kDistant;
-                    unsigned kf = kKeyInf;
-                    if (ord.on && nbf >= 0) {
-                        kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
-                        if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+                    if (gt < 32) {
+                        if (gt == 0) __stcg(P.tstate + g, (int)kSource);
+                        const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
+                        const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
+                        const bool act = prev == (int)kDistant;
+                        unsigned kf = kKeyInf;
+                        if (ord.on && nbf >= 0) {
+                            kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                            if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+                        }
+                        warp_push(ctl, cnt_next, out, P.n_tiles, act, nbf, ord.on ? kmin_next : nullptr, kf);
                     }
-                    warp_push(ctl, cnt_next, out, P.n_tiles, act, nbf, ord.on ? kmin_next : nullptr, kf);
                 }
             } else {
                 // faces where a node dropped, and (ordered) the smallest dropped value on each
@@ -261,23 +272,25 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Visi
                     warp_push(ctl, cnt_next, out, P.n_tiles, want, cand, ord.on ? kmin_next : nullptr, kc);
                 }
             }
+            group_sync(bid, GG::GT);                   // the visit is done with gc (and q, after the last)
         }
-        __syncthreads();                               // the queue is reused by the next piece
     }
 }
 
 template <class T, int BX, int BY, int BZ>
-__device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int it, int n,
-                                  unsigned kmin_cur, float width, int *s_visits, long long &st_tiles,
+__device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int it, int n,
+                                  unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
                                   long long &st_sweeps, long long &st_def) {
-    group_pass<T, BX, BY, BZ, false>(P, smbase, gcs, q, it, n, kmin_cur, width, s_visits, st_tiles, st_sweeps, st_def);
+    group_pass<T, BX, BY, BZ, false>(P, smbase, gcs, gqs, it, n, kmin_cur, width, chunk, s_visits, st_tiles,
+                                     st_sweeps, st_def);
 }
 
 template <class T, int BX, int BY, int BZ>
-__device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, VisitQueue &q, int r, int n,
-                                  unsigned kmin_cur, float width, int *s_visits, long long &st_tiles,
+__device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int r, int n,
+                                  unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
                                   long long &st_sweeps, long long &st_def) {
-    group_pass<T, BX, BY, BZ, true>(P, smbase, gcs, q, r, n, kmin_cur, width, s_visits, st_tiles, st_sweeps, st_def);
+    group_pass<T, BX, BY, BZ, true>(P, smbase, gcs, gqs, r, n, kmin_cur, width, chunk, s_visits, st_tiles,
+                                    st_sweeps, st_def);
 }
 
 }  // namespace eik

@@ -269,7 +269,7 @@ template <class T, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_persistent(FwdParams<T> P) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
-    __shared__ VisitQueue vq;
+    __shared__ GroupQueue gqs[GroupGeom<BX, BY, BZ>::NG];
     __shared__ int s_n, s_p, s_visits;
     __shared__ unsigned s_k;
     T *my = sm.phi[warp_in_cta()];
@@ -295,16 +295,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
         const int n = s_n;
         const unsigned kq = s_k;
         if (it > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
+        const int chunk = group_chunk(n, it > 0 ? s_p : 0, it > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
         n_prev = n;
         if (n == 0) break;
         if (it >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
         if (blockIdx.x == 0 && threadIdx.x == 0) {   // slot (it+2)%3 was last read in iteration it-1
             ctl->cnt[(it + 2) % 3] = 0;
             ctl->kmin[(it + 2) % 3] = kKeyInf;
+            ctl->grab[(it + 2) % 3] = 0;
             ctl->nproc[(it + 2) % 4] = 0;
         }
         if (n <= kGroupModeFactor * groups)
-            update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
+            update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits, t_upd,
+                                             sweeps, deferred);
         else
             update_pass<T, BX, BY, BZ>(P, my, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
         __syncthreads();
@@ -335,16 +338,19 @@ neighbour_check:
         const int n = s_n;
         const unsigned kq = s_k;
         if (r > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
+        const int chunk = group_chunk(n, r > 0 ? s_p : 0, r > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
         n_prev = n;
         if (n == 0) break;
         if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctl->rcnt[(r + 2) % 3] = 0;
             ctl->rkmin[(r + 2) % 3] = kKeyInf;
+            ctl->rgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
         if (n <= kGroupModeFactor * groups)
-            remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
+            remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits, t_rem,
+                                             sweeps, deferred);
         else
             remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
         __syncthreads();
@@ -380,22 +386,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                                                                               int prev_n) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
-    __shared__ VisitQueue vq;
+    __shared__ GroupQueue gqs[GroupGeom<BX, BY, BZ>::NG];
     __shared__ int s_visits;
     const int n = ld_volatile(&P.ctl->cnt[it % 3]);
     const unsigned kq = ld_volatile_u(&P.ctl->kmin[it % 3]);
     const float width = host_loop_width<BX, BY, BZ>(P.ctl, it, n, prev_n);
+    const int groups = (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG;
+    const int chunk = group_chunk(n, it > 0 ? ld_volatile(&P.ctl->nproc[(it - 1) % 4]) : 0, it > 0 ? prev_n : 0, groups,
+                                  GroupGeom<BX, BY, BZ>::GT);
     long long t = 0, s = 0, d = 0;
     init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
     if (threadIdx.x == 0) s_visits = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->cnt[(it + 2) % 3] = 0;
         P.ctl->kmin[(it + 2) % 3] = kKeyInf;
+        P.ctl->grab[(it + 2) % 3] = 0;
         P.ctl->nproc[(it + 2) % 4] = 0;
     }
     __syncthreads();
-    if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
-        update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, it, n, kq, width, &s_visits, t, s, d);
+    if (n <= kGroupModeFactor * groups)
+        update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits, t, s, d);
     else
         update_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], it, n, kq, width, &s_visits, t, s, d);
     __syncthreads();
@@ -417,22 +427,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                                                                               int prev_n) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
-    __shared__ VisitQueue vq;
+    __shared__ GroupQueue gqs[GroupGeom<BX, BY, BZ>::NG];
     __shared__ int s_visits;
     const int n = ld_volatile(&P.ctl->rcnt[r % 3]);
     const unsigned kq = ld_volatile_u(&P.ctl->rkmin[r % 3]);
     const float width = host_loop_width<BX, BY, BZ>(P.ctl, r, n, prev_n);
+    const int groups = (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG;
+    const int chunk = group_chunk(n, r > 0 ? ld_volatile(&P.ctl->nproc[(r - 1) % 4]) : 0, r > 0 ? prev_n : 0, groups,
+                                  GroupGeom<BX, BY, BZ>::GT);
     long long t = 0, s = 0, d = 0;
     init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
     if (threadIdx.x == 0) s_visits = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->rcnt[(r + 2) % 3] = 0;
         P.ctl->rkmin[(r + 2) % 3] = kKeyInf;
+        P.ctl->rgrab[(r + 2) % 3] = 0;
         P.ctl->nproc[(r + 2) % 4] = 0;
     }
     __syncthreads();
-    if (n <= kGroupModeFactor * (int)gridDim.x * GroupGeom<BX, BY, BZ>::NG)
-        remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, vq, r, n, kq, width, &s_visits, t, s, d);
+    if (n <= kGroupModeFactor * groups)
+        remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits, t, s, d);
     else
         remedy_pass<T, BX, BY, BZ>(P, sm.phi[warp_in_cta()], r, n, kq, width, &s_visits, t, s, d);
     __syncthreads();
