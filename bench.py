@@ -48,7 +48,19 @@ LAUNCHES_PER_SOLVE = 7
 # from the ncu capture summarised in profiles/k_persistent_oscillating256.md; reported only
 # while the kernel sources still hash to the captured version (else null).
 MEASURED_TRAFFIC = {
-    "oscillating_256": {"hash": "ccf4e34f36f0e199", "bytes": 374044672 + 94237952},
+    "oscillating_256": {"hash": "5df275c1ac9ad5b3", "bytes": 346479104 + 84680704},
+}
+
+
+# The paper's own timings (seconds on an NVIDIA Tesla P100; Tables 1, 2, 3 and 5,
+# Sec. 4.1) of its GPU FIM and iFIM for Examples 1, 2, 3 and 5 at N^2 nodes --
+# context for the B300 times of the same examples, not a target.
+PAPER_SIZES = (200, 500, 1000, 2000, 4000)
+PAPER_TIMES_S = {
+    1: {"fim": (0.00164, 0.00428, 0.08834, 0.32604, 1.67655), "ifim": (0.00141, 0.00384, 0.03721, 0.11642, 0.80981)},
+    2: {"fim": (0.00118, 0.00319, 0.08794, 0.63421, 1.86989), "ifim": (0.00097, 0.00329, 0.0539, 0.35359, 1.09434)},
+    3: {"fim": (0.00125, 0.00410, 0.08954, 0.78251, 2.05581), "ifim": (0.00089, 0.00341, 0.0499, 0.36897, 1.48971)},
+    5: {"fim": (0.00125, 0.00410, 0.08954, 0.78251, 2.45581), "ifim": (0.00119, 0.00341, 0.0689, 0.56897, 1.098971)},
 }
 
 
@@ -221,13 +233,15 @@ def run_ours(args, ws, rank, local):
 
         def step(stats=True):
             return api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp,
-                             out=phi, return_stats=stats, order=args.order, converge=args.converge)
+                             out=phi, return_stats=stats, order=args.order, converge=args.converge,
+                             method=args.method)
     else:
         probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h, i.src_val) for i in insts]
 
         def step(stats=True):
             return api.solve_batched(probs, tile=args.tile, schedule=args.schedule, workspace=wsp,
-                                     return_stats=stats, order=args.order, converge=args.converge)
+                                     return_stats=stats, order=args.order, converge=args.converge,
+                                     method=args.method)
 
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     for _ in range(args.warmup):
@@ -273,7 +287,7 @@ def run_ours(args, ws, rank, local):
             idx.copy_(idx_h, non_blocking=True)
             val.copy_(val_h, non_blocking=True)
             api.solve(F, idx, inst.h, val, tile=args.tile, schedule=args.schedule, workspace=wsp, out=phi,
-                      order=args.order, converge=args.converge)
+                      order=args.order, converge=args.converge, method=args.method)
             phi_h.copy_(phi, non_blocking=True)
             ev1.record(stream)
             ev1.synchronize()
@@ -300,7 +314,7 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "nodes_per_gpu": n_nodes, "instances": len(insts),
                        "tile": args.tile, "schedule": args.schedule, "order": args.order,
-                       "converge": args.converge,
+                       "converge": args.converge, "method": args.method,
                        "l2": "flushed between steps (256 MiB write outside the per-step events)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
@@ -314,8 +328,11 @@ def run_ours(args, ws, rank, local):
             step(stats=False)
         line["trace"] = tr.summary()
     if not args.no_extras:
+        if len(insts) == 1:
+            line["fim_vs_ifim"] = bench_methods(args, insts[0], F, idx, val, phi, wsp, flush_buf)
         line["batched"] = bench_batched(args, dev, wsp, flush_buf)
         line["adjoint"] = bench_adjoint(args, dev, wsp, flush_buf)
+        line["paper_examples"] = bench_paper_examples(args, dev, wsp, flush_buf)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import numpy as np
         import oracle
@@ -347,6 +364,48 @@ def _timed(fn, flush_buf, reps):
         ev1.synchronize()
         ms.append(ev0.elapsed_time(ev1))
     return statistics.median(ms)
+
+
+def bench_methods(args, inst, F, idx, val, phi, wsp, flush_buf):
+    """The same workload by the improved FIM (Algorithm 2) and by the FIM of Sec. 2.3
+    (tile-level neighbour checks, no remedy; unordered lists, as that method is
+    stated), both to the same discrete solution (cf. the paper's FIM-vs-iFIM
+    comparison, Sec. 4.2)."""
+    from paper_2106_15869_b300 import api
+    out = {}
+    for name, kw in (("ifim", dict(method="ifim")), ("fim", dict(method="fim", order=-1.0))):
+        run = lambda: api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, **kw)
+        run()
+        ms = _timed(run, flush_buf, 5)
+        _, st = api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, return_stats=True, **kw)
+        out[name] = {"ms": ms, "nodes_per_s": inst.n_nodes / (ms / 1e3),
+                     "iterations": st["iters_update"] + st["iters_remedy"],
+                     "tile_visits": st["tiles_update"] + st["tiles_remedy"], "sweeps": st["sweeps"]}
+    out["fim_speedup_over_ifim"] = out["ifim"]["ms"] / out["fim"]["ms"]
+    return out
+
+
+def bench_paper_examples(args, dev, wsp, flush_buf):
+    """Examples 1, 2, 3 and 5 of Sec. 4.1 (2D, [-10, 10]^2, N = 200 .. 4000) by both methods,
+    device time per solve, beside the paper's P100 times (Tables 1-3, 5)."""
+    import torch
+    from paper_2106_15869_b300 import api, workloads as W
+    rows = []
+    for ex in sorted(PAPER_TIMES_S):
+        for q, n in enumerate(PAPER_SIZES):
+            inst = W.paper_example_2d(ex, n=n)
+            F = torch.as_tensor(inst.F, dtype=torch.float32).to(dev)
+            idx = torch.as_tensor(inst.src_idx).to(dev)
+            val = torch.as_tensor(inst.src_val, dtype=torch.float32).to(dev)
+            phi = torch.empty_like(F)
+            row = {"example": ex, "n": n}
+            for name, kw in (("ifim", dict(method="ifim")), ("fim", dict(method="fim", order=-1.0))):
+                run = lambda: api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, **kw)
+                run()
+                row[f"{name}_ms"] = _timed(run, flush_buf, 3)
+                row[f"paper_p100_{name}_ms"] = 1e3 * PAPER_TIMES_S[ex][name][q]
+            rows.append(row)
+    return {"unit": "ms per solve (device time, FP32)", "rows": rows}
 
 
 def bench_batched(args, dev, wsp, flush_buf):
@@ -418,10 +477,13 @@ def main():
     ap.add_argument("--tile", default="auto")
     ap.add_argument("--schedule", default="auto")
     ap.add_argument("--converge", default="auto", choices=["auto", "confirm", "sweep"])
+    ap.add_argument("--method", default="ifim", choices=["ifim", "fim"],
+                    help="ifim: Algorithm 2 (the default); fim: the FIM of Sec. 2.3 at tile granularity")
     ap.add_argument("--order", type=float, default=0.0,
                     help="list order: 0 default bucketed, >0 bucket width, <0 unordered")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FIM comparison, batched, adjoint and paper-example measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
