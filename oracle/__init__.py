@@ -12,6 +12,7 @@ from a thread pool.
 
 Functions (each cites the passage it follows in its docstring):
   local_solve  exact root of eq. (6) from per-axis upwind minima
+  local_solve_aniso  the same with unequal spacings (Alg 1.2, corrected thresholds)
   fmm          fast marching (Sec. 2.1): the discrete solution
   gs           Gauss-Seidel sweeping (Sec. 2.2) to an exact fixed point
   ifim         Algorithm 2 (Steps 1-3) point by point
@@ -68,6 +69,14 @@ def _load():
         lib.eko_fim.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd, _i64, _pi64]
         lib.eko_residual.restype = _d
         lib.eko_residual.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd]
+        lib.eko_local_solve_aniso.restype = _d
+        lib.eko_local_solve_aniso.argtypes = [_d, _d, _d, _d, _d, _d, _d]
+        lib.eko_fmm_aniso.restype = _i64
+        lib.eko_fmm_aniso.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _pd, _pd, _pi64]
+        lib.eko_gs_aniso.restype = _i64
+        lib.eko_gs_aniso.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _pd, _pd, _i64]
+        lib.eko_residual_aniso.restype = _d
+        lib.eko_residual_aniso.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _pd, _pd]
         lib.eko_adjoint.restype = ctypes.c_int
         lib.eko_adjoint.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd, _pd, _pd]
         _lib = lib
@@ -97,6 +106,18 @@ def _src(src_idx, src_val):
     return idx, val
 
 
+def _spacing(h):
+    """h as a number (isotropic) or per axis (hx, hy[, hz]); returns (hx, hy, hz) or None."""
+    if np.ndim(h) == 0:
+        return None
+    hs = [float(v) for v in h]
+    if len(hs) == 2:
+        hs.append(hs[0])           # 2D: no z neighbours, hz unused
+    if len(hs) != 3:
+        raise ValueError("h must be a number or (hx, hy[, hz])")
+    return tuple(hs)
+
+
 def _p(a, t=_pd):
     return a.ctypes.data_as(t)
 
@@ -106,8 +127,15 @@ def local_solve(ax: float, ay: float, az: float, tau: float) -> float:
     return _load().eko_local_solve(float(ax), float(ay), float(az), float(tau))
 
 
+def local_solve_aniso(ax: float, ay: float, az: float, hx: float, hy: float, hz: float, F: float) -> float:
+    """Exact root of eq. (6) with spacings hx, hy, hz (Alg 1.2 with the validity thresholds)."""
+    return _load().eko_local_solve_aniso(float(ax), float(ay), float(az), float(hx), float(hy), float(hz), float(F))
+
+
 def fmm(F, h: float, src_idx, src_val=None, return_order: bool = False):
     """Fast marching (Sec. 2.1): the solution of eq. (4)/(6) with Dirichlet sources.
+
+    h: the spacing, or (hx, hy[, hz]) for unequal spacings (eq. 5/6 with dx, dy, dz).
 
     F: (ny, nx) or (nz, ny, nx) speeds (F == 0 impassable); src_idx: flat
     indices; src_val: values (default 0).  Returns phi (+inf where
@@ -118,8 +146,13 @@ def fmm(F, h: float, src_idx, src_val=None, return_order: bool = False):
     idx, val = _src(src_idx, src_val)
     phi = np.empty(F.shape, dtype=np.float64)
     order = np.empty(F.size, dtype=np.int64) if return_order else None
-    n = _load().eko_fmm(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(val),
-                        _p(phi), _p(order, _pi64) if order is not None else None)
+    hs = _spacing(h)
+    if hs is None:
+        n = _load().eko_fmm(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(val),
+                            _p(phi), _p(order, _pi64) if order is not None else None)
+    else:
+        n = _load().eko_fmm_aniso(nx, ny, nz, *hs, _p(F), idx.size, _p(idx, _pi64), _p(val),
+                                  _p(phi), _p(order, _pi64) if order is not None else None)
     if n < 0:
         raise ValueError("oracle fmm: invalid arguments")
     if return_order:
@@ -136,8 +169,13 @@ def gs(F, h: float, src_idx, src_val=None, max_rounds: int = 100000):
     nx, ny, nz = _dims(F)
     idx, val = _src(src_idx, src_val)
     phi = np.empty(F.shape, dtype=np.float64)
-    r = _load().eko_gs(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(val),
-                       _p(phi), int(max_rounds))
+    hs = _spacing(h)
+    if hs is None:
+        r = _load().eko_gs(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(val),
+                           _p(phi), int(max_rounds))
+    else:
+        r = _load().eko_gs_aniso(nx, ny, nz, *hs, _p(F), idx.size, _p(idx, _pi64), _p(val),
+                                 _p(phi), int(max_rounds))
     if r == -1:
         raise ValueError("oracle gs: invalid arguments")
     if r == -2:
@@ -187,14 +225,22 @@ def fim(F, h: float, src_idx, src_val=None, max_iters: int = 10**9):
 
 
 def residual(F, h: float, src_idx, phi, per_node: bool = False):
-    """max_p |sum_d ((phi_p - a_d)^+)^2 - tau_p^2| / tau_p^2 over non-source finite nodes (eq. 6)."""
+    """max_p |sum_d ((phi_p - a_d)^+)^2 - tau_p^2| / tau_p^2 over non-source finite nodes (eq. 6).
+
+    With h = (hx, hy[, hz]): |sum_d ((phi_p - a_d)^+ / h_d)^2 - 1/F_p^2| * F_p^2.
+    """
     F = _f64(F)
     nx, ny, nz = _dims(F)
     idx = np.ascontiguousarray(np.asarray(src_idx, dtype=np.int64).reshape(-1))
     phi = _f64(phi)
     res = np.empty(F.shape, dtype=np.float64) if per_node else None
-    m = _load().eko_residual(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(phi),
-                             _p(res) if res is not None else None)
+    hs = _spacing(h)
+    if hs is None:
+        m = _load().eko_residual(nx, ny, nz, float(h), _p(F), idx.size, _p(idx, _pi64), _p(phi),
+                                 _p(res) if res is not None else None)
+    else:
+        m = _load().eko_residual_aniso(nx, ny, nz, *hs, _p(F), idx.size, _p(idx, _pi64), _p(phi),
+                                       _p(res) if res is not None else None)
     return (m, res) if per_node else m
 
 

@@ -31,6 +31,9 @@
  *   eko_fim          the fast iterative method of Sec. 2.3 (with the
  *                    neighbour convergence check), point by point, same
  *                    two-phase semantics
+ *   eko_local_solve_aniso, eko_fmm_aniso, eko_gs_aniso, eko_residual_aniso
+ *                    the same with unequal spacings dx, dy, dz (eq. 5/6 as
+ *                    written with them; Alg 1.2 with the validity thresholds)
  *   eko_residual     max relative residual of eq. (6) over non-source nodes
  *   eko_adjoint      transposed upwind-linearised system solved by back
  *                    substitution in increasing-phi order (adjoint-state
@@ -97,14 +100,76 @@ static inline double tau_of(double h, double F) {
     return F > 0.0 ? h / F : EKO_INF;
 }
 
-/* local solve at node p from the current values phi */
-static double solve_at(const dims_t *d, const double *phi, int64_t p, double tau) {
+/*
+ * Exact root u of eq. (6) with unequal spacings (eq. 5 in 2D as written with
+ * dx, dy; Alg 1.2):  sum_d ((u - a_d)^+ / h_d)^2 = 1 / F^2.  The axes with
+ * a_d < u at the root are a prefix of the axes sorted by a_d (g(u) = the left
+ * side is increasing), so with (a_d, h_d) sorted by a_d:
+ *   one-sided   u = a1 + h1 / F                                   valid iff u <= a2
+ *   two-sided   u = (a1 h2^2 + a2 h1^2 + h1 h2 sqrt((h1^2 + h2^2)/F^2 - (a1-a2)^2))
+ *                   / (h1^2 + h2^2)                               valid iff u <= a3
+ *   three-sided with w_d = 1/h_d^2, W = sum w_d:
+ *               u = (sum w_d a_d + sqrt(W/F^2 - sum_{i<j} w_i w_j (a_i-a_j)^2)) / W
+ * (the two-sided form is Alg 1.2's; its printed switch at |a1-a2| >
+ * sqrt(dx^2+dy^2)/F is where the discriminant vanishes, not where the root
+ * stops being valid).  F <= 0 or a1 = +inf gives +inf.
+ */
+double eko_local_solve_aniso(double ax, double ay, double az, double hx, double hy, double hz, double F) {
+    double a[3] = {ax, ay, az}, h[3] = {hx, hy, hz};
+    /* sort (a, h) pairs by a */
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2 - p; ++q)
+            if (a[q] > a[q + 1]) {
+                double t = a[q]; a[q] = a[q + 1]; a[q + 1] = t;
+                t = h[q]; h[q] = h[q + 1]; h[q + 1] = t;
+            }
+    if (!(F > 0.0) || isinf(a[0])) return EKO_INF;
+    double s = 1.0 / F;
+    double u = a[0] + h[0] * s;
+    if (u <= a[1]) return u;
+    double h1s = h[0] * h[0], h2s = h[1] * h[1], d12 = a[0] - a[1];
+    u = (a[0] * h2s + a[1] * h1s + h[0] * h[1] * sqrt((h1s + h2s) * s * s - d12 * d12)) / (h1s + h2s);
+    if (u <= a[2]) return u;
+    double w[3] = {1.0 / h1s, 1.0 / h2s, 1.0 / (h[2] * h[2])};
+    double W = w[0] + w[1] + w[2];
+    double sa = w[0] * a[0] + w[1] * a[1] + w[2] * a[2];
+    double cross = 0.0;
+    for (int p = 0; p < 3; ++p)
+        for (int q = p + 1; q < 3; ++q) cross += w[p] * w[q] * (a[p] - a[q]) * (a[p] - a[q]);
+    double disc = W * s * s - cross;
+    if (disc < 0.0) disc = 0.0; /* >= 0 in exact arithmetic on this branch */
+    return (sa + sqrt(disc)) / W;
+}
+
+/* grid spacings; iso = all equal (the isotropic cascade of eko_local_solve is used) */
+typedef struct {
+    double hx, hy, hz;
+    int iso;
+} spacing_t;
+
+static spacing_t iso_spacing(double h) {
+    spacing_t sp = {h, h, h, 1};
+    return sp;
+}
+
+static spacing_t make_spacing(double hx, double hy, double hz) {
+    spacing_t sp = {hx, hy, hz, hx == hy && hy == hz};
+    return sp;
+}
+
+static int check_spacing(const spacing_t *sp) {
+    return !(sp->hx > 0.0 && sp->hy > 0.0 && sp->hz > 0.0) || isinf(sp->hx) || isinf(sp->hy) || isinf(sp->hz);
+}
+
+/* local solve at node p (speed Fp) from the current values phi */
+static double solve_at(const dims_t *d, const double *phi, int64_t p, const spacing_t *sp, double Fp) {
     int64_t i, j, k;
     unflat(d, p, &i, &j, &k);
     double ax = dmin(nbval(d, phi, i - 1, j, k), nbval(d, phi, i + 1, j, k));
     double ay = dmin(nbval(d, phi, i, j - 1, k), nbval(d, phi, i, j + 1, k));
     double az = dmin(nbval(d, phi, i, j, k - 1), nbval(d, phi, i, j, k + 1));
-    return eko_local_solve(ax, ay, az, tau);
+    if (sp->iso) return eko_local_solve(ax, ay, az, tau_of(sp->hx, Fp));
+    return eko_local_solve_aniso(ax, ay, az, sp->hx, sp->hy, sp->hz, Fp);
 }
 
 /* neighbour list: up to 6 in-grid face neighbours */
@@ -216,11 +281,11 @@ static int64_t heap_pop(heap_t *H) {
  * order_out (nullable) receives the acceptance order; returns the number of
  * accepted nodes (finite phi), or -1 on an argument error.
  */
-int64_t eko_fmm(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
-                int64_t n_src, const int64_t *src_idx, const double *src_val,
-                double *phi, int64_t *order_out) {
+static int64_t fmm_impl(int64_t nx, int64_t ny, int64_t nz, spacing_t sp, const double *F,
+                        int64_t n_src, const int64_t *src_idx, const double *src_val,
+                        double *phi, int64_t *order_out) {
     dims_t d = {nx, ny, nz};
-    if (check_args(&d, h, F, n_src, src_idx, src_val)) return -1;
+    if (check_args(&d, sp.hx, F, n_src, src_idx, src_val) || check_spacing(&sp)) return -1;
     int64_t N = nx * ny * nz;
     unsigned char *is_src = malloc((size_t)N);
     unsigned char *accepted = calloc((size_t)N, 1);
@@ -246,7 +311,7 @@ int64_t eko_fmm(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
         for (int q = 0; q < nn; ++q) {
             int64_t r = nb[q];
             if (accepted[r] || is_src[r]) continue;
-            double u = solve_at(&d, known, r, tau_of(h, F[r]));
+            double u = solve_at(&d, known, r, &sp, F[r]);
             if (u < phi[r]) {
                 phi[r] = u;
                 heap_push_or_decrease(&H, r);
@@ -257,6 +322,19 @@ int64_t eko_fmm(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
     return n_acc;
 }
 
+int64_t eko_fmm(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
+                int64_t n_src, const int64_t *src_idx, const double *src_val,
+                double *phi, int64_t *order_out) {
+    return fmm_impl(nx, ny, nz, iso_spacing(h), F, n_src, src_idx, src_val, phi, order_out);
+}
+
+/* fast marching with spacings hx, hy, hz (equal spacings take the isotropic cascade) */
+int64_t eko_fmm_aniso(int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, const double *F,
+                      int64_t n_src, const int64_t *src_idx, const double *src_val,
+                      double *phi, int64_t *order_out) {
+    return fmm_impl(nx, ny, nz, make_spacing(hx, hy, hz), F, n_src, src_idx, src_val, phi, order_out);
+}
+
 /*
  * Gauss-Seidel with alternating sweep orders (Sec. 2.2): in 2D the four
  * orders (i up/down) x (j up/down); in 3D the eight analogous orders.  Each
@@ -265,11 +343,11 @@ int64_t eko_fmm(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
  * Returns the number of rounds, or -1 on an argument error, or -2 when
  * max_rounds is reached.
  */
-int64_t eko_gs(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
-               int64_t n_src, const int64_t *src_idx, const double *src_val,
-               double *phi, int64_t max_rounds) {
+static int64_t gs_impl(int64_t nx, int64_t ny, int64_t nz, spacing_t sp, const double *F,
+                       int64_t n_src, const int64_t *src_idx, const double *src_val,
+                       double *phi, int64_t max_rounds) {
     dims_t d = {nx, ny, nz};
-    if (check_args(&d, h, F, n_src, src_idx, src_val)) return -1;
+    if (check_args(&d, sp.hx, F, n_src, src_idx, src_val) || check_spacing(&sp)) return -1;
     int64_t N = nx * ny * nz;
     unsigned char *is_src = malloc((size_t)N);
     init_sources(N, phi, is_src, n_src, src_idx, src_val);
@@ -290,7 +368,7 @@ int64_t eko_gs(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
                         int64_t i = rx ? nx - 1 - ii : ii;
                         int64_t p = flat(&d, i, j, k);
                         if (is_src[p]) continue;
-                        double u = solve_at(&d, phi, p, tau_of(h, F[p]));
+                        double u = solve_at(&d, phi, p, &sp, F[p]);
                         if (u < phi[p]) { phi[p] = u; changed = 1; }
                     }
                 }
@@ -299,6 +377,18 @@ int64_t eko_gs(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
     }
     free(is_src);
     return rounds;
+}
+
+int64_t eko_gs(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
+               int64_t n_src, const int64_t *src_idx, const double *src_val,
+               double *phi, int64_t max_rounds) {
+    return gs_impl(nx, ny, nz, iso_spacing(h), F, n_src, src_idx, src_val, phi, max_rounds);
+}
+
+int64_t eko_gs_aniso(int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, const double *F,
+                     int64_t n_src, const int64_t *src_idx, const double *src_val,
+                     double *phi, int64_t max_rounds) {
+    return gs_impl(nx, ny, nz, make_spacing(hx, hy, hz), F, n_src, src_idx, src_val, phi, max_rounds);
 }
 
 /*
@@ -324,6 +414,7 @@ int eko_ifim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
              int64_t n_src, const int64_t *src_idx, const double *src_val,
              double *phi, int skip_remedy, int64_t max_iters, int64_t *stats) {
     dims_t d = {nx, ny, nz};
+    spacing_t sp = iso_spacing(h);
     if (check_args(&d, h, F, n_src, src_idx, src_val)) return -1;
     int64_t N = nx * ny * nz;
     unsigned char *is_fixed = malloc((size_t)N);
@@ -352,7 +443,7 @@ int eko_ifim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
         if (st[0] >= max_iters) { rc = -2; goto done; }
         st[0]++;
         for (int64_t a = 0; a < n; ++a)
-            cand[a] = solve_at(&d, phi, list[a], tau_of(h, F[list[a]]));
+            cand[a] = solve_at(&d, phi, list[a], &sp, F[list[a]]);
         int64_t m = 0;
         for (int64_t a = 0; a < n; ++a) {
             int64_t p = list[a];
@@ -384,7 +475,7 @@ int eko_ifim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
         n = 0;
         for (int64_t p = 0; p < N; ++p) {
             if (is_fixed[p]) continue;
-            double u = solve_at(&d, phi, p, tau_of(h, F[p]));
+            double u = solve_at(&d, phi, p, &sp, F[p]);
             if (u < phi[p]) list[n++] = p;
         }
         st[2] = n;
@@ -392,7 +483,7 @@ int eko_ifim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
             if (st[1] >= max_iters) { rc = -2; goto done; }
             st[1]++;
             for (int64_t a = 0; a < n; ++a)
-                cand[a] = solve_at(&d, phi, list[a], tau_of(h, F[list[a]]));
+                cand[a] = solve_at(&d, phi, list[a], &sp, F[list[a]]);
             int64_t m = 0;
             for (int64_t a = 0; a < n; ++a) {
                 int64_t p = list[a];
@@ -440,6 +531,7 @@ int eko_fim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
             int64_t n_src, const int64_t *src_idx, const double *src_val,
             double *phi, int64_t max_iters, int64_t *stats) {
     dims_t d = {nx, ny, nz};
+    spacing_t sp = iso_spacing(h);
     if (check_args(&d, h, F, n_src, src_idx, src_val)) return -1;
     int64_t N = nx * ny * nz;
     unsigned char *is_fixed = malloc((size_t)N);
@@ -464,7 +556,7 @@ int eko_fim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
         if (st[0] >= max_iters) { rc = -2; goto done; }
         st[0]++;
         for (int64_t a = 0; a < n; ++a)
-            cand[a] = solve_at(&d, phi, list[a], tau_of(h, F[list[a]]));
+            cand[a] = solve_at(&d, phi, list[a], &sp, F[list[a]]);
         int64_t m = 0;
         for (int64_t a = 0; a < n; ++a) {
             int64_t p = list[a];
@@ -474,7 +566,7 @@ int eko_fim(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
                 for (int q = 0; q < nn; ++q) {
                     int64_t r = nb[q];
                     if (is_fixed[r] || (lab[r] & 5)) continue;
-                    double u = solve_at(&d, phi, r, tau_of(h, F[r]));
+                    double u = solve_at(&d, phi, r, &sp, F[r]);
                     if (u < phi[r]) {
                         phi[r] = u;
                         lab[r] |= 4;
@@ -506,9 +598,10 @@ done:
  * returns the maximum.  Nodes with finite phi but tau = +inf (impassable and
  * not a source) count as an infinite residual.
  */
-double eko_residual(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
-                    int64_t n_src, const int64_t *src_idx, const double *phi, double *res) {
+static double residual_impl(int64_t nx, int64_t ny, int64_t nz, spacing_t sp, const double *F,
+                            int64_t n_src, const int64_t *src_idx, const double *phi, double *res) {
     dims_t d = {nx, ny, nz};
+    const double hd[3] = {sp.hx, sp.hy, sp.hz};
     int64_t N = nx * ny * nz;
     unsigned char *is_src = calloc((size_t)N, 1);
     for (int64_t s = 0; s < n_src; ++s)
@@ -517,9 +610,23 @@ double eko_residual(int64_t nx, int64_t ny, int64_t nz, double h, const double *
     for (int64_t p = 0; p < N; ++p) {
         double r = 0.0;
         if (!is_src[p] && isfinite(phi[p])) {
-            double tau = tau_of(h, F[p]);
+            double tau = tau_of(sp.hx, F[p]);
             if (isinf(tau)) {
                 r = EKO_INF;
+            } else if (!sp.iso) {
+                /* sum_d ((phi - a_d)^+ / h_d)^2 against 1 / F^2 */
+                int64_t i, j, k;
+                unflat(&d, p, &i, &j, &k);
+                double a[3];
+                a[0] = dmin(nbval(&d, phi, i - 1, j, k), nbval(&d, phi, i + 1, j, k));
+                a[1] = dmin(nbval(&d, phi, i, j - 1, k), nbval(&d, phi, i, j + 1, k));
+                a[2] = dmin(nbval(&d, phi, i, j, k - 1), nbval(&d, phi, i, j, k + 1));
+                double sum = 0.0, s2 = 1.0 / (F[p] * F[p]);
+                for (int q = 0; q < 3; ++q) {
+                    double t = (phi[p] - a[q]) / hd[q];
+                    if (t > 0.0) sum += t * t;
+                }
+                r = fabs(sum - s2) / s2;
             } else {
                 int64_t i, j, k;
                 unflat(&d, p, &i, &j, &k);
@@ -540,6 +647,16 @@ double eko_residual(int64_t nx, int64_t ny, int64_t nz, double h, const double *
     }
     free(is_src);
     return worst;
+}
+
+double eko_residual(int64_t nx, int64_t ny, int64_t nz, double h, const double *F,
+                    int64_t n_src, const int64_t *src_idx, const double *phi, double *res) {
+    return residual_impl(nx, ny, nz, iso_spacing(h), F, n_src, src_idx, phi, res);
+}
+
+double eko_residual_aniso(int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, const double *F,
+                          int64_t n_src, const int64_t *src_idx, const double *phi, double *res) {
+    return residual_impl(nx, ny, nz, make_spacing(hx, hy, hz), F, n_src, src_idx, phi, res);
 }
 
 /* ------------------------------------------------------------------ */

@@ -324,3 +324,96 @@ def test_adjoint_matches_central_finite_differences(seed):
         fd.append((loss((1 / sp).reshape(phi.shape)) - loss((1 / sm).reshape(phi.shape))) / (2 * eps))
     fd = np.array(fd)
     assert np.linalg.norm(g[cells] - fd) <= 1e-5 * max(np.linalg.norm(fd), 1e-12)
+
+
+# ---------------------------------------------------------------- unequal spacings (Alg 1.2, eq. 5/6 with dx, dy, dz)
+def test_aniso_local_solve_closed_forms():
+    inf = np.inf
+    # two-sided, a_x = a_y = 0, dx = 1, dy = 2, F = 1: u^2 + (u/2)^2 = 1
+    assert abs(oracle.local_solve_aniso(0, 0, inf, 1, 2, 1, 1) - 2 / np.sqrt(5)) < 1e-15
+    # three-sided, all minima 0, spacings 1, 2, 3: u^2 (1 + 1/4 + 1/9) = 1, u = 6/7
+    assert abs(oracle.local_solve_aniso(0, 0, 0, 1, 2, 3, 1) - 6 / 7) < 1e-15
+    # one-sided along x, valid: u = a_x + dx / F
+    assert oracle.local_solve_aniso(0, 5, inf, 1, 1, 1, 2) == 0.5
+    # the printed switch of Alg 1.2 (|a_x - a_y| > sqrt(dx^2 + dy^2) / F) would take the
+    # two-sided root here, which lies below a_x; the valid root is one-sided along y
+    assert oracle.local_solve_aniso(1.5, 0, inf, 2, 1, 1, 1) == 1.0
+    assert oracle.local_solve_aniso(1.2, 0, inf, 1, 1, 1, 1) == 1.0
+    # the smallest minimum with a large spacing does not win alone
+    u = oracle.local_solve_aniso(0, 2.5, inf, 3, 0.1, 1, 1)
+    assert 2.5 < u < 3.0
+    assert abs((u / 3) ** 2 + ((u - 2.5) / 0.1) ** 2 - 1) < 1e-12
+
+
+def test_aniso_local_solve_satisfies_eq6_and_bounds():
+    rng = np.random.default_rng(17)
+    for _ in range(3000):
+        a = rng.uniform(0, 2, 3)
+        if rng.random() < 0.3:
+            a[rng.integers(0, 3)] = np.inf
+        h = rng.uniform(0.05, 3.0, 3)
+        F = rng.uniform(0.1, 10.0)
+        u = oracle.local_solve_aniso(*a, *h, F)
+        t = np.maximum(u - a, 0.0) / h
+        assert abs(np.sum(t * t) * F * F - 1.0) < 1e-11
+        # upper bound: the best one-sided root; lower bound: the smallest minimum
+        assert u <= np.min(a + h / F) * (1 + 1e-14) and u > np.min(a)
+
+
+def test_aniso_local_solve_reduces_to_isotropic_and_scales():
+    rng = np.random.default_rng(23)
+    for _ in range(2000):
+        a = rng.uniform(0, 2, 3)
+        h = rng.uniform(0.05, 2.0)
+        F = rng.uniform(0.1, 10.0)
+        iso = oracle.local_solve(*a, h / F)
+        assert abs(oracle.local_solve_aniso(*a, h, h, h, F) - iso) <= 1e-14 * max(1.0, iso)
+        hs = rng.uniform(0.05, 2.0, 3)
+        c = rng.uniform(0.1, 10.0)
+        u = oracle.local_solve_aniso(*a, *hs, F)
+        assert abs(oracle.local_solve_aniso(*(c * a), *(c * hs), F) - c * u) <= 1e-13 * max(1.0, c * u)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_aniso_fmm_equals_gauss_seidel(seed):
+    inst = W.random_small(500 + seed, max_edge=11, p_barrier=0.08 if seed % 3 == 0 else 0.0)
+    rng = np.random.default_rng(seed)
+    hs = tuple(rng.uniform(0.05, 2.0, 3))
+    phi = oracle.fmm(inst.F, hs, inst.src_idx, inst.src_val)
+    gs, _ = oracle.gs(inst.F, hs, inst.src_idx, inst.src_val)
+    fin = np.isfinite(phi)
+    assert np.array_equal(fin, np.isfinite(gs))
+    scale = max(1.0, float(np.max(np.abs(phi[fin]))) if fin.any() else 1.0)
+    assert np.max(np.abs(phi[fin] - gs[fin]), initial=0) <= 1e-13 * scale
+    assert oracle.residual(inst.F, hs, inst.src_idx, phi) <= 1e-11
+
+
+def test_aniso_axis_exactness_and_isotropic_case():
+    F = np.ones((9, 11, 13))
+    hs = (0.3, 0.7, 1.9)
+    phi = oracle.fmm(F, hs, [0])
+    k = np.arange(13)
+    assert np.allclose(phi[0, 0, :], k * hs[0], rtol=1e-15, atol=0)
+    assert np.allclose(phi[0, :, 0], np.arange(11) * hs[1], rtol=1e-15, atol=0)
+    assert np.allclose(phi[:, 0, 0], np.arange(9) * hs[2], rtol=1e-15, atol=0)
+    inst = W.random_small(77, dims=(7, 6, 5), three_d=True)
+    assert np.array_equal(oracle.fmm(inst.F, (inst.h,) * 3, inst.src_idx, inst.src_val),
+                          oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val))
+
+
+def test_aniso_refinement_toward_euclidean_distance():
+    """A disc source of radius 0.25 on [0, 1] x [0, 2] with dy = 2 dx: the error
+    against the distance to the circle falls by about 2 per halving."""
+    errs = []
+    for n in (33, 65, 129):
+        hx, hy = 1.0 / (n - 1), 2.0 / (n - 1)
+        x = np.arange(n) * hx
+        y = np.arange(n) * hy
+        X, Y = np.meshgrid(x, y)
+        d = np.hypot(X - 0.5, Y - 1.0) - 0.25
+        near = d <= max(hx, hy)
+        idx = np.flatnonzero(near.reshape(-1))
+        val = np.maximum(d.reshape(-1)[idx], 0.0)
+        phi = oracle.fmm(np.ones((n, n)), (hx, hy), idx, val)
+        errs.append(float(np.max(np.abs(phi - np.maximum(d, 0.0)))))
+    assert 1.6 < errs[0] / errs[1] < 2.6 and 1.6 < errs[1] / errs[2] < 2.6, errs
