@@ -96,10 +96,15 @@ extern "C" {
 #define EIK_FP32 0
 #define EIK_FP64 1
 
-/* one grid: nx, ny, nz >= 1 nodes; isotropic spacing h > 0 */
+/* one grid: nx, ny, nz >= 1 nodes; spacing h > 0 along x, and hy, hz along
+ * y and z (0 = h: the square mesh of Alg 1.1 / Alg 1.3).  Unequal spacings
+ * solve eq. (5)/(6) as written with dx, dy, dz (Alg 1.2, with the validity
+ * thresholds); all grids of one call must have the same ratios hy/h and hz/h
+ * (hz is ignored when nz == 1), and the adjoint takes equal spacings only. */
 typedef struct {
     int64_t nx, ny, nz;
     double h;
+    double hy, hz;
 } eik_grid;
 
 /* per-call options; a zero-filled struct (or NULL) selects the defaults */

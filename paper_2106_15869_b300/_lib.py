@@ -26,7 +26,7 @@ METHODS = {"ifim": 0, "fim": 1}
 
 class eik_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
-                ("h", ctypes.c_double)]
+                ("h", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
 
 
 class eik_options(ctypes.Structure):
@@ -134,11 +134,24 @@ def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=Fal
     return o
 
 
+def spacing(h):
+    """h as a number or per axis (hx, hy[, hz]) -> (h, hy, hz) of eik_grid (0 = same as h)."""
+    if isinstance(h, (int, float)) or getattr(h, "ndim", 1) == 0:
+        return float(h), 0.0, 0.0
+    hs = [float(v) for v in h]
+    if len(hs) == 2:
+        hs.append(0.0)
+    if len(hs) != 3:
+        raise ValueError("h must be a number or (hx, hy[, hz])")
+    return hs[0], hs[1], hs[2]
+
+
 def grids_array(dims_h):
-    """[(nx, ny, nz, h), ...] -> ctypes array of eik_grid."""
+    """[(nx, ny, nz, h), ...] -> ctypes array of eik_grid; h a number or (hx, hy[, hz])."""
     arr = (eik_grid * len(dims_h))()
     for q, (nx, ny, nz, h) in enumerate(dims_h):
-        arr[q].nx, arr[q].ny, arr[q].nz, arr[q].h = int(nx), int(ny), int(nz), float(h)
+        arr[q].nx, arr[q].ny, arr[q].nz = int(nx), int(ny), int(nz)
+        arr[q].h, arr[q].hy, arr[q].hz = spacing(h)
     return arr
 
 

@@ -81,7 +81,8 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
 
     F: (ny, nx) or (nz, ny, nx) float32 (or float64 = FP64 validation mode)
     speeds, F == 0 impassable; src_idx: flat indices; src_val: values
-    (default 0); h: grid spacing.  Returns phi with F's shape, dtype and device
+    (default 0); h: grid spacing, or (hx, hy[, hz]) for unequal spacings
+    (eq. 5/6 with dx, dy, dz).  Returns phi with F's shape, dtype and device
     (+inf where unreachable); with return_stats also a dict of run statistics
     (this synchronises the stream).  order: 0 = default bucketed list order,
     > 0 = bucket width in tile-crossing times, < 0 = unordered lists (every

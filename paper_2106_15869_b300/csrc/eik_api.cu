@@ -106,13 +106,22 @@ struct Layout {
     long long n_tiles;
     unsigned long long q_slots;
     std::vector<InstDesc> desc_host;
+    double cy = 1.0, cz = 1.0;   // axis weights (dx/dy)^2, (dx/dz)^2 shared by the call's grids
+    bool aniso = false;
 };
+
+// spacing along y and z of a grid (0 = h)
+inline double spacing_y(const eik_grid &g) { return g.hy != 0.0 ? g.hy : g.h; }
+inline double spacing_z(const eik_grid &g) { return g.hz != 0.0 ? g.hz : g.h; }
+inline bool spacing_ok(double v) { return v == 0.0 || (v > 0.0 && v < 1e300); }
 
 bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std::string *why) {
     const TileShape ts = tile_shape(o.tile);
     const size_t esz = o.precision == EIK_FP64 ? 8 : 4;
     const long long V = (long long)ts.bx * ts.by * ts.bz;
     L.desc_host.resize((size_t)B);
+    L.cy = L.cz = 1.0;
+    bool have_cy = false, have_cz = false;
     long long tiles = 0;
     for (int64_t b = 0; b < B; ++b) {
         const eik_grid &g = grids[b];
@@ -123,6 +132,21 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
         if (!(g.h > 0.0) || !(g.h < 1e300)) {
             if (why) *why = "grid " + std::to_string(b) + ": h must be finite and > 0";
             return false;
+        }
+        if (!spacing_ok(g.hy) || !spacing_ok(g.hz)) {
+            if (why) *why = "grid " + std::to_string(b) + ": hy, hz must be 0 or finite and > 0";
+            return false;
+        }
+        {
+            // axis weights, compared over the grids that have that axis
+            const double ry = g.h / spacing_y(g), rz = g.h / spacing_z(g);
+            const double cyb = ry * ry, czb = rz * rz;
+            if ((g.ny > 1 && have_cy && cyb != L.cy) || (g.nz > 1 && have_cz && czb != L.cz)) {
+                if (why) *why = "grid " + std::to_string(b) + ": all grids of one call must have the same hy/h and hz/h";
+                return false;
+            }
+            if (g.ny > 1 && !have_cy) { L.cy = cyb; have_cy = true; }
+            if (g.nz > 1 && !have_cz) { L.cz = czb; have_cz = true; }
         }
         InstDesc &d = L.desc_host[(size_t)b];
         std::memset(&d, 0, sizeof(d));
@@ -138,6 +162,7 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
             return false;
         }
     }
+    L.aniso = L.cy != 1.0 || L.cz != 1.0;
     L.n_tiles = tiles;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
@@ -272,6 +297,9 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.max_iters = o.max_iters > 0 ? o.max_iters : auto_max_iters(L);
     P.skip_remedy = o.skip_remedy;
     P.fim = o.method == EIK_METHOD_FIM ? 1 : 0;
+    P.mt.cy = (T)L.cy;
+    P.mt.cz = (T)L.cz;
+    P.mt.aniso = L.aniso ? 1 : 0;
     P.one_visit = o.converge == EIK_CONVERGE_SWEEP ? 1 : 0;
     P.max_sweeps = 4 * (BX + BY + BZ) + 8;
     P.F = static_cast<const T *>(F);
@@ -479,6 +507,10 @@ struct AdjLayout {
 bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout &L, std::string *why) {
     Layout fl;   // reuse the forward's dims/tile checks and descriptors
     if (!make_layout(B, grids, o, fl, why)) return false;
+    if (fl.aniso) {
+        if (why) *why = "the adjoint takes equal spacings (hy = hz = h)";
+        return false;
+    }
     const TileShape ts = tile_shape(o.tile);
     const size_t esz = o.precision == EIK_FP64 ? 8 : 4;
     const long long V = (long long)ts.bx * ts.by * ts.bz;

@@ -158,7 +158,7 @@ __device__ void async_update_phase(const FwdParams<T> &P, const AsyncQ &Q, T *sm
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
         bool changed;
-        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
+        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, P.mt, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         __threadfence();
         __syncwarp();
@@ -194,7 +194,7 @@ __device__ void async_remedy_phase(const FwdParams<T> &P, const AsyncQ &Q, T *sm
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
         bool changed;
-        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
+        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, P.mt, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         __threadfence();
         __syncwarp();
@@ -229,7 +229,7 @@ __device__ void async_detect_pass(const FwdParams<T> &P, const AsyncQ &Q, T *sm,
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                low |= sweep_solve(ax, ay, az, tau[m]) < v[m];
+                low |= node_solve(ax, ay, az, tau[m], P.mt) < v[m];
             }
         }
         if (__any_sync(kFull, low) && lane == 0) {

@@ -186,6 +186,76 @@ __device__ __forceinline__ double sweep_solve(double ax, double ay, double az, d
     return local_solve<double>(ax, ay, az, tau);
 }
 
+// Unequal spacings (eq. 5/6 with dx, dy, dz; Alg 1.2).  With tau = dx / F and
+// axis weights c_d = (dx / h_d)^2 (c_x = 1) the equation is
+//   sum_d c_d ((u - a_d)^+)^2 = tau^2,
+// solved by the same prefix cascade over the minima sorted by value, each
+// minimum carrying its weight (d2 = a2 - a1, d3 = a3 - a1, C = c1 + c2 + c3):
+//   one-sided   u = a1 + tau / sqrt(c1)                                       valid iff u <= a2
+//   two-sided   u = a1 + (c2 d2 + sqrt((c1 + c2) tau^2 - c1 c2 d2^2)) / (c1 + c2)   valid iff u <= a3
+//   three-sided u = a1 + (c2 d2 + c3 d3 + sqrt(C tau^2 - c1 c2 d2^2 - c1 c3 d3^2 - c2 c3 (d3 - d2)^2)) / C
+// The weights are per call (every grid of a call has the same spacing ratios).
+template <class T>
+struct Metric {
+    T cy, cz;     // (dx / dy)^2, (dx / dz)^2
+    int aniso;    // 0: equal spacings, the isotropic cascade
+};
+
+// compare-exchange of (minimum, weight) pairs by minimum
+template <class T>
+__device__ __forceinline__ void cx_pair(T &a, T &c, T &b, T &e) {
+    const bool sw = b < a;
+    const T a0 = a, c0 = c;
+    a = sw ? b : a; c = sw ? e : c;
+    b = sw ? a0 : b; e = sw ? c0 : e;
+}
+
+template <class T>
+__device__ __forceinline__ T local_solve_w(T ax, T ay, T az, T tau, T cy, T cz) {
+    T a1 = ax, c1 = T(1), a2 = ay, c2 = cy, a3 = az, c3 = cz;
+    cx_pair(a1, c1, a2, c2);
+    cx_pair(a2, c2, a3, c3);
+    cx_pair(a1, c1, a2, c2);
+    T u = a1 + tau / vsqrt(c1);
+    if (u <= a2) return u;
+    const T d2 = a2 - a1, t2 = tau * tau, C2 = c1 + c2;
+    u = a1 + (c2 * d2 + vsqrt(vmax(C2 * t2 - c1 * c2 * d2 * d2, T(0)))) / C2;
+    if (u <= a3) return u;
+    const T d3 = a3 - a1, d32 = d3 - d2, C3 = C2 + c3;
+    T disc = C3 * t2 - (c1 * c2 * d2 * d2 + c1 * c3 * d3 * d3 + c2 * c3 * d32 * d32);
+    disc = vmax(disc, T(0));
+    return a1 + (c2 * d2 + c3 * d3 + vsqrt(disc)) / C3;
+}
+
+// FP32 sweep form of local_solve_w: the three candidate roots at once, then
+// the selection (as local_solve_fast).
+__device__ __forceinline__ float local_solve_fast_w(float ax, float ay, float az, float tau, float cy, float cz) {
+    float a1 = ax, c1 = 1.0f, a2 = ay, c2 = cy, a3 = az, c3 = cz;
+    cx_pair(a1, c1, a2, c2);
+    cx_pair(a2, c2, a3, c3);
+    cx_pair(a1, c1, a2, c2);
+    const float t2 = tau * tau, C2 = c1 + c2, C3 = C2 + c3;
+    const float d2 = a2 - a1, d3 = a3 - a1, d32 = d3 - d2;
+    const float u1 = a1 + tau * rsqrtf(c1);
+    const float u2 = a1 + (c2 * d2 + sqrt_approx(C2 * t2 - c1 * c2 * d2 * d2)) / C2;
+    const float u3 =
+        a1 + (c2 * d2 + c3 * d3 + sqrt_approx(C3 * t2 - (c1 * c2 * d2 * d2 + c1 * c3 * d3 * d3 + c2 * c3 * d32 * d32))) / C3;
+    return u1 <= a2 ? u1 : (u2 <= a3 ? u2 : u3);
+}
+
+__device__ __forceinline__ float sweep_solve_w(float ax, float ay, float az, float tau, float cy, float cz) {
+    return local_solve_fast_w(ax, ay, az, tau, cy, cz);
+}
+__device__ __forceinline__ double sweep_solve_w(double ax, double ay, double az, double tau, double cy, double cz) {
+    return local_solve_w<double>(ax, ay, az, tau, cy, cz);
+}
+
+// The root every relaxation uses: isotropic cascade, or the weighted one.
+template <class T>
+__device__ __forceinline__ T node_solve(T ax, T ay, T az, T tau, const Metric<T> &mt) {
+    return mt.aniso ? sweep_solve_w(ax, ay, az, tau, mt.cy, mt.cz) : sweep_solve(ax, ay, az, tau);
+}
+
 // Device-wide barrier for a cooperative launch.  Every wait is bounded by
 // kWaitLimitNs; on a timeout the block raises ctl->abort and every block
 // leaves at its next barrier.  Returns false when the launch must stop.

@@ -51,6 +51,7 @@ struct FwdParams {
     T *phi_t, *tau_t;
     Ctl *ctl;
     long long max_iters;
+    Metric<T> mt;                // axis weights of unequal spacings
     int skip_remedy;
     int fim;                     // 1 = the fast iterative method of Sec. 2.3 (one neighbour-check loop)
     int one_visit;               // Step 2: a visit whose relaxation converged moves the tile to Source
@@ -185,7 +186,7 @@ __device__ __forceinline__ unsigned spread_slots(unsigned M) {
 template <class T, int BX, int BY, int BZ>
 __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NPL],
                                           const T (&tau)[TileGeom<BX, BY, BZ>::NPL], int max_sweeps,
-                                          unsigned &mine, bool &first_changed) {
+                                          const Metric<T> &mt, unsigned &mine, bool &first_changed) {
     using G = TileGeom<BX, BY, BZ>;
     const int lane = lane_id();
     mine = 0;
@@ -201,7 +202,7 @@ __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NP
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = sweep_solve(ax, ay, az, tau[m]);
+                const T u = node_solve(ax, ay, az, tau[m], mt);
                 if (u < v[m]) { v[m] = u; sm[c] = u; ch |= 1u << m; }
             }
         }
@@ -326,7 +327,7 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
         bool changed;
-        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
+        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, P.mt, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         if (lane == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
         if (changed && (!P.one_visit || s >= P.max_sweeps)) {
@@ -380,7 +381,7 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
                 const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = sweep_solve(ax, ay, az, tau[m]);
+                const T u = node_solve(ax, ay, az, tau[m], P.mt);
                 if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
             }
         }
@@ -441,7 +442,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         unsigned mine;
         bool changed;
-        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, mine, changed);
+        const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, P.mt, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         const int fm = changed_faces<BX, BY, BZ>(mine);
         if (lane == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }

@@ -87,7 +87,7 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
                 const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
                 const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
                 const T az = vmin(sm[c[m] - G::SX * G::SY], sm[c[m] + G::SX * G::SY]);
-                const T u = sweep_solve(ax, ay, az, tau[m]);
+                const T u = node_solve(ax, ay, az, tau[m], P.mt);
                 if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
             }
         }

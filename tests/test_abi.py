@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported():
 
 def test_struct_sizes_match_header_layout():
     # int64 x3 + double; int32,int32,int64,int32,int32,float,int32[3]; 7 int64 + 2 int32 + 2 double
-    assert ctypes.sizeof(_lib.eik_grid) == 32
+    assert ctypes.sizeof(_lib.eik_grid) == 48
     assert ctypes.sizeof(_lib.eik_options) == 40
     assert ctypes.sizeof(_lib.eik_stats) == 7 * 8 + 2 * 4 + 2 * 8
 
@@ -66,6 +66,29 @@ def test_workspace_size_rules():
     assert _ws_size((5, 5, 5, 0.0)) == 0
     assert _ws_size((5, 5, 5, float("nan"))) == 0
     assert _ws_size((5, 5, 5, 1.0), precision=7) == 0
+    # unequal spacings: hy, hz must be 0 (= h) or finite and > 0
+    assert _ws_size((5, 5, 5, (1.0, 2.0, 3.0))) > 0
+    assert _ws_size((5, 5, 5, (1.0, -2.0, 3.0))) == 0
+    assert _ws_size((5, 5, 5, (1.0, 2.0, float("nan")))) == 0
+    assert _ws_size((5, 5, 5, (1.0, 2.0, float("inf")))) == 0
+
+
+def test_spacing_ratio_rules():
+    lib = _lib.load()
+    o = _lib.make_options()
+    # every grid of one call shares hy/h and hz/h (the axis weights are per call)
+    same = _lib.grids_array([(8, 8, 8, (0.1, 0.2, 0.3)), (9, 7, 5, (0.2, 0.4, 0.6))])
+    assert lib.eik_workspace_size_batched(2, same, ctypes.byref(o)) > 0
+    diff = _lib.grids_array([(8, 8, 8, (0.1, 0.2, 0.3)), (9, 7, 5, (0.2, 0.2, 0.6))])
+    assert lib.eik_workspace_size_batched(2, diff, ctypes.byref(o)) == 0
+    # a 2D grid has no z axis: its hz does not enter the comparison
+    mixed = _lib.grids_array([(8, 8, 1, (0.1, 0.2, 5.0)), (9, 7, 5, (0.2, 0.4, 0.6))])
+    assert lib.eik_workspace_size_batched(2, mixed, ctypes.byref(o)) > 0
+    # equal spacings given explicitly are the isotropic case; the adjoint takes only those
+    iso = _lib.grids_array([(8, 8, 8, (0.1, 0.1, 0.1))])
+    assert lib.eik_adjoint_workspace_size_batched(1, iso, ctypes.byref(o)) > 0
+    aniso = _lib.grids_array([(8, 8, 8, (0.1, 0.2, 0.1))])
+    assert lib.eik_adjoint_workspace_size_batched(1, aniso, ctypes.byref(o)) == 0
 
 
 def test_host_argument_errors_before_device_work():

@@ -381,3 +381,74 @@ def test_fim_mode_batched():
     assert st["status"] == 0
     for inst, phi in zip(insts, phis):
         assert_parity(phi.cpu().numpy(), oracle_phi(inst, "fp64"), TOL64)
+
+
+# ------------------------------------------------------------------ unequal spacings (Alg 1.2, eq. 5/6 with dx, dy, dz)
+def _aniso_case(seed, dims, hs, three_d=True):
+    inst = W.random_small(seed, dims=dims, three_d=three_d, f_lo=0.2, f_hi=5.0, max_src=3)
+    return inst, hs
+
+
+def _gpu_solve_h(inst, h, dtype, **kw):
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    tdt = torch.float32 if dtype == "fp32" else torch.float64
+    F = torch.as_tensor(inst.F, dtype=tdt).cuda()
+    phi, st = api.solve(F, inst.src_idx, h, inst.src_val, return_stats=True, **kw)
+    assert st["status"] == 0, st
+    return phi.cpu().double().numpy()
+
+
+def _oracle_h(inst, h, dtype):
+    F = inst.F.astype(np.float32).astype(np.float64) if dtype == "fp32" else inst.F
+    val = inst.src_val.astype(np.float32).astype(np.float64) if dtype == "fp32" else inst.src_val
+    return oracle.fmm(F, h, inst.src_idx, val)
+
+
+@pytest.mark.parametrize("tile", ["8x8x8", "4x4x4", "8x8x4"])
+@pytest.mark.parametrize("method", ["ifim", "fim"])
+def test_unequal_spacings_3d(tile, method):
+    inst, hs = _aniso_case(41, (37, 29, 23), (0.05, 0.11, 0.023))
+    for dt, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        # the oracle gets the spacings in single precision for the FP32 run: only arithmetic differs
+        h_or = tuple(float(np.float32(v)) for v in hs) if dt == "fp32" else hs
+        got = _gpu_solve_h(inst, hs, dt, tile=tile, method=method)
+        assert_parity(got, _oracle_h(inst, h_or, dt), tol)
+
+
+@pytest.mark.parametrize("schedule", ["hostloop", "async"])
+def test_unequal_spacings_schedules(schedule):
+    inst, hs = _aniso_case(43, (33, 21, 19), (1.0, 0.4, 2.5))
+    got = _gpu_solve_h(inst, hs, "fp64", schedule=schedule)
+    assert_parity(got, _oracle_h(inst, hs, "fp64"), TOL64)
+
+
+def test_unequal_spacings_2d_and_axis_exactness():
+    inst, hs = _aniso_case(47, (70, 45, 1), (0.3, 0.07), three_d=False)
+    for dt, tol in (("fp64", TOL64), ("fp32", TOL32)):
+        h_or = tuple(float(np.float32(v)) for v in hs) if dt == "fp32" else hs
+        got = _gpu_solve_h(inst, hs, dt)
+        assert_parity(got, _oracle_h(inst, h_or, dt), tol)
+    # F = 1, corner source: phi along the axes is k dx and k dy
+    one = W.point_source_2d(64, (0, 0))
+    got = _gpu_solve_h(one, (0.5, 2.0), "fp64")
+    assert np.allclose(got[0, :], 0.5 * np.arange(64), rtol=1e-14, atol=0)
+    assert np.allclose(got[:, 0], 2.0 * np.arange(64), rtol=1e-14, atol=0)
+
+
+def test_unequal_spacings_batched_and_adjoint_rejects():
+    torch = _torch()
+    from paper_2106_15869_b300 import api, _lib
+    a, _ = _aniso_case(51, (20, 17, 13), None)
+    b, _ = _aniso_case(52, (15, 22, 9), None)
+    ha, hb = (0.1, 0.3, 0.2), (0.05, 0.15, 0.1)            # same ratios
+    probs = [(torch.as_tensor(a.F).cuda(), a.src_idx, ha, torch.as_tensor(a.src_val).cuda()),
+             (torch.as_tensor(b.F).cuda(), b.src_idx, hb, torch.as_tensor(b.src_val).cuda())]
+    phis = api.solve_batched(probs)
+    assert_parity(phis[0].cpu().numpy(), oracle.fmm(a.F, ha, a.src_idx, a.src_val), TOL64)
+    assert_parity(phis[1].cpu().numpy(), oracle.fmm(b.F, hb, b.src_idx, b.src_val), TOL64)
+    with pytest.raises(_lib.EikonalError):
+        api.solve_batched([probs[0], (probs[1][0], b.src_idx, (0.05, 0.1, 0.1))])
+    r = torch.ones_like(phis[0])
+    with pytest.raises(_lib.EikonalError):
+        api.adjoint(probs[0][0], a.src_idx, ha, phis[0], r)
