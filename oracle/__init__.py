@@ -18,6 +18,7 @@ Functions (each cites the passage it follows in its docstring):
   ifim         Algorithm 2 (Steps 1-3) point by point
   fim          the fast iterative method of Sec. 2.3 point by point
   residual     relative residual of eq. (6)
+  backtrace    shortest-path back-trace by steepest descent on phi (Example 4)
   adjoint      d(loss)/d(slowness) by back substitution on the upwind
                linearisation of eq. (6) (adjoint-state method; not in the paper)
 """
@@ -77,6 +78,8 @@ def _load():
         lib.eko_gs_aniso.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _pd, _pd, _i64]
         lib.eko_residual_aniso.restype = _d
         lib.eko_residual_aniso.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _pd, _pd]
+        lib.eko_backtrace.restype = ctypes.c_int
+        lib.eko_backtrace.argtypes = [_i64, _i64, _i64, _d, _d, _d, _pd, _i64, _pi64, _i64, _pi64, _pi64]
         lib.eko_adjoint.restype = ctypes.c_int
         lib.eko_adjoint.argtypes = [_i64, _i64, _i64, _d, _pd, _i64, _pi64, _pd, _pd, _pd, _pd]
         _lib = lib
@@ -242,6 +245,26 @@ def residual(F, h: float, src_idx, phi, per_node: bool = False):
         m = _load().eko_residual_aniso(nx, ny, nz, *hs, _p(F), idx.size, _p(idx, _pi64), _p(phi),
                                        _p(res) if res is not None else None)
     return (m, res) if per_node else m
+
+
+def backtrace(phi, h, start_idx, max_len: int = 100000):
+    """Shortest paths by steepest descent on the phi map (Example 4, Sec. 4.1).
+
+    phi: (ny, nx) or (nz, ny, nx) arrival times (any float dtype; compared in
+    float64); h: spacing or (hx, hy[, hz]); start_idx: flat start nodes.
+    Returns a list of int64 arrays of flat node ids, start first.
+    """
+    phi = _f64(phi)
+    nx, ny, nz = _dims(phi)
+    hs = _spacing(h) or (float(h),) * 3
+    st = np.ascontiguousarray(np.asarray(start_idx, dtype=np.int64).reshape(-1))
+    out = np.empty((st.size, int(max_len)), dtype=np.int64)
+    ln = np.empty(st.size, dtype=np.int64)
+    rc = _load().eko_backtrace(nx, ny, nz, *hs, _p(phi), st.size, _p(st, _pi64), int(max_len),
+                               _p(out, _pi64), _p(ln, _pi64))
+    if rc != 0:
+        raise ValueError("oracle backtrace: invalid arguments")
+    return [out[q, :ln[q]].copy() for q in range(st.size)]
 
 
 def adjoint(F, h: float, src_idx, phi, r, return_lambda: bool = False):

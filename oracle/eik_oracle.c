@@ -35,6 +35,8 @@
  *                    the same with unequal spacings dx, dy, dz (eq. 5/6 as
  *                    written with them; Alg 1.2 with the validity thresholds)
  *   eko_residual     max relative residual of eq. (6) over non-source nodes
+ *   eko_backtrace    shortest-path back-trace by steepest descent on the phi
+ *                    map over the 26 (8 in 2D) neighbours (Example 4)
  *   eko_adjoint      transposed upwind-linearised system solved by back
  *                    substitution in increasing-phi order (adjoint-state
  *                    traveltime method, Leung & Qian 2006); not in the paper
@@ -660,6 +662,67 @@ double eko_residual_aniso(int64_t nx, int64_t ny, int64_t nz, double hx, double 
 }
 
 /* ------------------------------------------------------------------ */
+/*
+ * Shortest-path back-trace by descent on the phi map (the application of
+ * Example 4, Sec. 4.1; the paper names gradient descent without stating the
+ * discrete rule, so this is the steepest descent on the grid graph):
+ * from the start node, repeatedly move to the neighbour among the 26 (8 in
+ * 2D) adjacent nodes with the steepest descent slope
+ *     (phi[nb] - phi[cur]) / |x_nb - x_cur|      (physical distance, spacings hx, hy, hz)
+ * among the neighbours with phi[nb] < phi[cur]; ties go to the lower flat
+ * index.  The slope is formed in double as (phi[nb] - phi[cur]) * (1 / len),
+ * with 1 / len = 1 / sqrt(dx^2 + dy^2 + dz^2) of the offset.  The path stops
+ * at a node with no lower neighbour (a source or a local minimum) or after
+ * max_len nodes.  phi = +inf at the start gives an empty path.
+ * path_out: [n_paths][max_len] node ids (entries past len are -1);
+ * len_out: [n_paths].  Returns 0, or -1 on an argument error.
+ */
+int eko_backtrace(int64_t nx, int64_t ny, int64_t nz, double hx, double hy, double hz, const double *phi,
+                  int64_t n_paths, const int64_t *start_idx, int64_t max_len, int64_t *path_out,
+                  int64_t *len_out) {
+    dims_t d = {nx, ny, nz};
+    spacing_t sp = make_spacing(hx, hy, hz);
+    if (nx < 1 || ny < 1 || nz < 1 || check_spacing(&sp) || n_paths < 0 || max_len < 1) return -1;
+    int64_t N = nx * ny * nz;
+    for (int64_t q = 0; q < n_paths; ++q)
+        if (start_idx[q] < 0 || start_idx[q] >= N) return -1;
+    for (int64_t q = 0; q < n_paths; ++q) {
+        int64_t *row = path_out + q * max_len;
+        for (int64_t t = 0; t < max_len; ++t) row[t] = -1;
+        int64_t cur = start_idx[q], len = 0;
+        if (!isinf(phi[cur])) {
+            row[len++] = cur;
+            while (len < max_len) {
+                int64_t i, j, k;
+                unflat(&d, cur, &i, &j, &k);
+                int64_t best = -1;
+                double best_slope = 0.0;
+                for (int dk = -1; dk <= 1; ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            if (!di && !dj && !dk) continue;
+                            int64_t a = i + di, b = j + dj, c = k + dk;
+                            if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                            int64_t nb = flat(&d, a, b, c);
+                            if (!(phi[nb] < phi[cur])) continue;
+                            double ox = di * hx, oy = dj * hy, oz = dk * hz;
+                            double inv_len = 1.0 / sqrt(ox * ox + oy * oy + oz * oz);
+                            double slope = (phi[nb] - phi[cur]) * inv_len;
+                            if (best < 0 || slope < best_slope || (slope == best_slope && nb < best)) {
+                                best = nb;
+                                best_slope = slope;
+                            }
+                        }
+                if (best < 0) break;
+                cur = best;
+                row[len++] = cur;
+            }
+        }
+        len_out[q] = len;
+    }
+    return 0;
+}
+
 /* ordering helper for the adjoint: sort node ids by (phi, id) */
 static const double *g_sort_key;
 static int cmp_by_phi(const void *x, const void *y) {

@@ -417,3 +417,51 @@ def test_aniso_refinement_toward_euclidean_distance():
         phi = oracle.fmm(np.ones((n, n)), (hx, hy), idx, val)
         errs.append(float(np.max(np.abs(phi - np.maximum(d, 0.0)))))
     assert 1.6 < errs[0] / errs[1] < 2.6 and 1.6 < errs[1] / errs[2] < 2.6, errs
+
+
+# ---------------------------------------------------------------- shortest-path back-trace (Example 4)
+def test_backtrace_axis_and_diagonal_paths():
+    """F = 1, source at the corner: descent from an axis node runs along the
+    axis, from a diagonal node along the diagonal (the steepest discrete slope)."""
+    phi2 = oracle.fmm(np.ones((24, 24)), 1.0, [0])
+    for k in range(1, 24):
+        assert list(oracle.backtrace(phi2, 1.0, [k])[0]) == list(range(k, -1, -1))
+        assert list(oracle.backtrace(phi2, 1.0, [k * 24])[0]) == [m * 24 for m in range(k, -1, -1)]
+        assert list(oracle.backtrace(phi2, 1.0, [k * 25])[0]) == [m * 25 for m in range(k, -1, -1)]
+    phi3 = oracle.fmm(np.ones((12, 12, 12)), 0.5, [0])
+    for k in range(1, 12):
+        diag = k * (1 + 12 + 144)
+        assert list(oracle.backtrace(phi3, 0.5, [diag])[0]) == [m * 157 for m in range(k, -1, -1)]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_backtrace_paths_descend_to_a_source(seed):
+    inst = W.random_small(700 + seed, max_edge=14, p_barrier=0.1 if seed % 2 else 0.0)
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+    nx, ny, nz = inst.dims
+    rng = np.random.default_rng(seed)
+    starts = rng.integers(0, phi.size, size=20)
+    flat = phi.reshape(-1)
+    src = set(int(s) for s in inst.src_idx)
+    for st, path in zip(starts, oracle.backtrace(phi, inst.h, starts)):
+        if not np.isfinite(flat[st]):
+            assert path.size == 0
+            continue
+        assert path[0] == st and int(path[-1]) in src
+        assert np.all(np.diff(flat[path]) < 0)                          # strictly descending
+        i, j, k = path % nx, (path // nx) % ny, path // (nx * ny)
+        steps = np.stack([np.diff(i), np.diff(j), np.diff(k)])
+        assert np.all(np.abs(steps) <= 1) and np.all(np.abs(steps).sum(0) >= 1)   # 26-neighbours
+
+
+def test_backtrace_length_close_to_the_straight_segment():
+    """F = 1: the path is at least as long as the straight segment to the source
+    and, made of 26-neighbour steps, at most 20 % longer."""
+    n = 40
+    phi = oracle.fmm(np.ones((n, n, n)), 1.0, [0])
+    rng = np.random.default_rng(3)
+    starts = rng.integers(0, n ** 3, size=40)
+    for st, path in zip(starts, oracle.backtrace(phi, 1.0, starts)):
+        p = np.stack([path % n, (path // n) % n, path // (n * n)], 1).astype(float)
+        L = np.sum(np.linalg.norm(np.diff(p, axis=0), axis=1))
+        assert np.linalg.norm(p[0]) - 1e-12 <= L <= 1.2 * np.linalg.norm(p[0]) + 1e-12
