@@ -330,6 +330,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_extras:
         if len(insts) == 1:
             line["fim_vs_ifim"] = bench_methods(args, insts[0], F, idx, val, phi, wsp, flush_buf)
+            line["backtrace"] = bench_backtrace(args, insts[0], F, idx, val, phi, wsp, flush_buf)
         line["batched"] = bench_batched(args, dev, wsp, flush_buf)
         line["adjoint"] = bench_adjoint(args, dev, wsp, flush_buf)
         line["paper_examples"] = bench_paper_examples(args, dev, wsp, flush_buf)
@@ -383,6 +384,23 @@ def bench_methods(args, inst, F, idx, val, phi, wsp, flush_buf):
                      "tile_visits": st["tiles_update"] + st["tiles_remedy"], "sweeps": st["sweeps"]}
     out["fim_speedup_over_ifim"] = out["ifim"]["ms"] / out["fim"]["ms"]
     return out
+
+
+def bench_backtrace(args, inst, F, idx, val, phi, wsp, flush_buf):
+    """Shortest paths from 4096 seeded destinations back to the source by steepest
+    descent on the solved phi (the application of Example 4, Sec. 4.1)."""
+    import numpy as np
+    import torch
+    from paper_2106_15869_b300 import api
+    api.solve(F, idx, inst.h, val, workspace=wsp, out=phi)
+    starts = torch.as_tensor(np.random.default_rng(11).integers(0, inst.n_nodes, size=4096)).to(phi.device)
+    max_len = 4 * sum(F.shape)
+    run = lambda: api.backtrace(phi, starts, inst.h, max_len=max_len)
+    _, length = run()
+    ms = _timed(run, flush_buf, 5)
+    steps = int(length.clamp(min=0).sum().item())
+    return {"paths": 4096, "max_len": max_len, "ms": ms, "path_nodes": steps,
+            "path_nodes_per_s": steps / (ms / 1e3), "mean_length": steps / 4096}
 
 
 def bench_paper_examples(args, dev, wsp, flush_buf):

@@ -211,6 +211,31 @@ int eik_adjoint(const eik_grid *grid, const void *F, const void *phi, const int6
                 const eik_options *opt, eik_stats *stats);
 
 /*
+ * Shortest paths by descent on an arrival-time map (the application of
+ * Example 4, Sec. 4.1: from a destination back to the source).  The paper
+ * names gradient descent on phi without the discrete rule; this is the
+ * steepest descent on the grid graph: the next node is the neighbour among
+ * the 26 (8 when nz == 1) adjacent nodes with the smallest slope
+ * (phi[nb] - phi[cur]) / |x_nb - x_cur| (physical distance with the grid's
+ * spacings) among those with phi[nb] < phi[cur], evaluated in double; ties go
+ * to the lower flat index.  A path ends at a node without a lower neighbour
+ * (a source, for a phi from eik_solve) or when its row is full.
+ *   grid       host; dims and spacings (h, hy, hz as for eik_solve)
+ *   precision  EIK_FP32 / EIK_FP64: the element type of phi
+ *   phi        device [nz][ny][nx] arrival times (e.g. eik_solve's output)
+ *   start_idx  device [n_paths] int64 flat start nodes
+ *   max_len    nodes per row of `path` (>= 1; n_paths * max_len <= 2^34)
+ *   path       device [n_paths][max_len] int64 output: node ids, start first,
+ *              -1 past the end of the path
+ *   len        device [n_paths] int64 output: nodes on each path; 0 when phi
+ *              is +inf at the start (unreachable), -1 when the start index is
+ *              outside the grid
+ * Asynchronous on `stream`; argument errors are returned before any launch.
+ */
+int eik_backtrace(const eik_grid *grid, int precision, const void *phi, const int64_t *start_idx, int64_t n_paths,
+                  int64_t max_len, int64_t *path, int64_t *len, void *stream);
+
+/*
  * eik_solve without any device allocation and without a workspace argument.
  * The paper has no counterpart: this is for callers that must not allocate
  * device memory at solve time -- e.g. a latency-critical loop that cannot

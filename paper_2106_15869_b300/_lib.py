@@ -112,6 +112,9 @@ def _optional_symbols(lib):
     if hasattr(lib, "eik_adjoint"):
         lib.eik_adjoint.restype = ctypes.c_int
         lib.eik_adjoint.argtypes = [G, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp, O, S]
+    if hasattr(lib, "eik_backtrace"):
+        lib.eik_backtrace.restype = ctypes.c_int
+        lib.eik_backtrace.argtypes = [G, ctypes.c_int, _vp, _vp, _i64, _i64, _vp, _vp, _vp]
 
 
 def check(rc: int):

@@ -264,6 +264,35 @@ def adjoint(F, src_idx, h, phi, r, **kw):
     return adjoint_batched([(F, src_idx, h)], [phi], [r], **kw)[0]
 
 
+def backtrace(phi: torch.Tensor, start_idx, h, max_len: int = 65536):
+    """Shortest paths from start nodes back to the source by steepest descent on
+    the arrival-time map phi (Example 4, Sec. 4.1; the rule is in eik_backtrace's
+    header comment).
+
+    phi: (ny, nx) or (nz, ny, nx) CUDA tensor, float32 or float64 (e.g. solve's
+    output); start_idx: flat start nodes; h: spacing or (hx, hy[, hz]).
+    Returns (path, length): path int64 (n_paths, max_len) of flat node ids,
+    start first, -1 past the end; length int64 (n_paths,) (0: unreachable start).
+    """
+    if phi.dtype not in _DT or not phi.is_cuda:
+        raise TypeError("phi must be a float32/float64 CUDA tensor")
+    phi = phi.contiguous()
+    nx, ny, nz = _dims(phi)
+    dev = phi.device
+    st = _as_index(start_idx, dev)
+    n = st.numel()
+    path = torch.empty((n, int(max_len)), dtype=torch.int64, device=dev)
+    length = torch.empty(n, dtype=torch.int64, device=dev)
+    g = _lib.grids_array([(nx, ny, nz, h)])
+    with torch.cuda.device(dev):
+        rc = _lib.load().eik_backtrace(g, _lib.PRECISIONS[_DT[phi.dtype]], phi.data_ptr(),
+                                       st.data_ptr() if n else None, n, int(max_len),
+                                       path.data_ptr() if n else None, length.data_ptr() if n else None,
+                                       _stream_ptr())
+        _lib.check(rc)
+    return path, length
+
+
 class EikonalFn(torch.autograd.Function):
     """phi = EikonalFn.apply(s, sources, h): arrival times for slowness s = 1/F.
 

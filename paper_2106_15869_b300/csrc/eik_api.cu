@@ -3,6 +3,7 @@
 // tile shape, and the two loop schedules (persistent cooperative launch, or
 // one launch per iteration with a host-read list size).
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include "eik_kernels.cuh"
 #include "eik_async.cuh"
 #include "eik_adjoint.cuh"
+#include "eik_backtrace.cuh"
 
 using namespace eik;
 
@@ -746,6 +748,42 @@ int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_id
     // block, per-tile state, keys, lists), so stale contents of the shared
     // array from an earlier call do not matter
     return eik_solve(grid, F, src_idx, src_val, n_src, phi, scratch, kNoAllocScratchBytes, stream, opt, stats);
+}
+
+int eik_backtrace(const eik_grid *grid, int precision, const void *phi, const int64_t *start_idx, int64_t n_paths,
+                  int64_t max_len, int64_t *path, int64_t *len, void *stream) {
+    if (!grid || !phi) return fail(EIK_ERR_ARG, "null grid or phi");
+    const eik_grid &g = *grid;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > (1ll << 30) || g.ny > (1ll << 30) || g.nz > (1ll << 30))
+        return fail(EIK_ERR_ARG, "dims must be in [1, 2^30]");
+    if (!(g.h > 0.0) || !(g.h < 1e300) || !spacing_ok(g.hy) || !spacing_ok(g.hz))
+        return fail(EIK_ERR_ARG, "h must be finite and > 0; hy, hz 0 or finite and > 0");
+    if (precision != EIK_FP32 && precision != EIK_FP64) return fail(EIK_ERR_ARG, "unknown precision");
+    if (n_paths < 0 || n_paths > (1ll << 28)) return fail(EIK_ERR_ARG, "n_paths must be in [0, 2^28]");
+    if (max_len < 1 || max_len > (1ll << 34) / std::max<int64_t>(n_paths, 1))
+        return fail(EIK_ERR_ARG, "max_len must be >= 1 and n_paths * max_len <= 2^34");
+    if (n_paths == 0) return EIK_OK;
+    if (!start_idx || !path || !len) return fail(EIK_ERR_ARG, "null start_idx, path or len");
+    BacktraceConst bc;
+    const double hx = g.h, hy = spacing_y(g), hz = spacing_z(g);
+    for (int l = 0; l < 26; ++l) {
+        const int c = l < 13 ? l : l + 1;
+        const double ox = (c % 3 - 1) * hx, oy = ((c / 3) % 3 - 1) * hy, oz = (c / 9 - 1) * hz;
+        const double sq = ox * ox + oy * oy + oz * oz;
+        bc.inv_len[l] = 1.0 / std::sqrt(sq);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned blocks = (unsigned)((n_paths * 32 + 255) / 256);
+    const long long *si = reinterpret_cast<const long long *>(start_idx);
+    long long *po = reinterpret_cast<long long *>(path), *lo = reinterpret_cast<long long *>(len);
+    if (precision == EIK_FP64)
+        k_backtrace<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(phi), (int)g.nx, (int)g.ny, (int)g.nz,
+                                                    bc, si, n_paths, max_len, po, lo);
+    else
+        k_backtrace<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(phi), (int)g.nx, (int)g.ny, (int)g.nz,
+                                                   bc, si, n_paths, max_len, po, lo);
+    EIK_CUDA(cudaGetLastError(), "k_backtrace launch");
+    return EIK_OK;
 }
 
 int eik_set_trace(void *device_buffer, int64_t capacity) {

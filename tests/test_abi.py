@@ -131,3 +131,18 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libeikonal.so"))
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_backtrace_argument_errors_before_device_work():
+    lib = _lib.load()
+    g = _lib.grids_array([(8, 8, 8, 0.1)])
+    E = _lib.EIK_ERR_ARG
+    assert lib.eik_backtrace(g, 0, None, 1, 1, 4, 1, 1, None) == E                     # null phi
+    assert lib.eik_backtrace(g, 7, 1, 1, 1, 4, 1, 1, None) == E                        # precision
+    assert lib.eik_backtrace(g, 0, 1, 1, -1, 4, 1, 1, None) == E                       # n_paths
+    assert lib.eik_backtrace(g, 0, 1, 1, 1, 0, 1, 1, None) == E                        # max_len
+    assert lib.eik_backtrace(g, 0, 1, None, 1, 4, 1, 1, None) == E                     # null starts
+    assert lib.eik_backtrace(g, 0, 1, 1, 1 << 20, 1 << 20, 1, 1, None) == E            # buffer too large
+    bad = _lib.grids_array([(8, 8, 8, (0.1, -1.0, 0.1))])
+    assert lib.eik_backtrace(bad, 0, 1, 1, 1, 4, 1, 1, None) == E                      # spacing
+    assert lib.eik_backtrace(g, 0, 1, None, 0, 4, None, None, None) == _lib.EIK_OK     # nothing to do
