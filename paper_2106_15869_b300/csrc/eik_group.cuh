@@ -2,9 +2,9 @@
 //
 // In an iteration with a short list (the usual case in Step 2, where the
 // Active set is a thin band) the iteration time is the latency of one tile
-// visit, not throughput.  There, a group of GT threads (GT = min(V, 128))
-// owns a tile with V/GT nodes per thread (1 to 4), so a sweep costs a few
-// local solves plus a named barrier instead of V/32 solves in a row;
+// visit, not throughput.  There, a group of GT threads (GT = min(V, 256))
+// owns a tile with V/GT nodes per thread (1 or 2), so a sweep costs one or
+// two local solves plus a named barrier instead of V/32 solves in a row;
 // the group's OR-barrier is the convergence flag.  The rules applied are
 // exactly those of the warp passes in eik_forward.cuh; an iteration uses one
 // mode or the other for all its tiles (every CTA sees the same list size).
@@ -14,9 +14,11 @@
 
 namespace eik {
 
-// threads per latency-mode group: at most kGroupThreads, so that a CTA holds
-// several groups and an iteration keeps more tiles in flight
-constexpr int kGroupThreads = 128;
+// threads per latency-mode group (at most a CTA).  Measured on B300: 256
+// threads (one node per thread for 16x16x1 tiles, two for 8x8x8) against 128
+// is 1.3-1.5x faster on 2D grids and equal on 3D; 64 is slower on both.
+constexpr int kGroupThreads = 256;
+static_assert(kGroupThreads <= 32 * kWarpsPerCta, "a group fits in a CTA");
 
 template <int BX, int BY, int BZ>
 struct GroupGeom {
