@@ -38,6 +38,14 @@
 
 namespace eik {
 
+// threads per adjoint group: 128 (four nodes per thread on 8x8x8 tiles).  The
+// adjoint's visits are cheaper than the forward's and more of them run at
+// once; measured on the 192^3 tomography batch, 256-thread groups are 1.2x
+// slower.
+constexpr int kAdjGroupThreads = 128;
+template <int BX, int BY, int BZ>
+using AdjGroupGeom = GroupGeom<BX, BY, BZ, kAdjGroupThreads>;
+
 template <class T>
 struct AdjParams {
     const InstDesc *desc;       // in_off: F offset; out_off: phi and r offset; aux_off: gradient offset
@@ -207,7 +215,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
                                          int gt, int bid, unsigned &mine, bool &first_changed) {
     using G = TileGeom<BX, BY, BZ>;
     using A = AdjGeom<BX, BY, BZ>;
-    using GG = GroupGeom<BX, BY, BZ>;
+    using GG = AdjGroupGeom<BX, BY, BZ>;
     constexpr int NPT = GG::NPT;
     const T INF = Num<T>::inf();
     T lam[NPT], rr[NPT], tau[NPT], J[NPT], w[NPT][6];
@@ -316,14 +324,14 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
 template <class T, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    using GG = GroupGeom<BX, BY, BZ>;
+    using GG = AdjGroupGeom<BX, BY, BZ>;
     extern __shared__ __align__(16) unsigned char adj_smem_raw[];
     AdjSmem<T, BX, BY, BZ> *sms = reinterpret_cast<AdjSmem<T, BX, BY, BZ> *>(adj_smem_raw);
     __shared__ int s_n, s_p, s_visits;
     __shared__ unsigned s_k;
-    __shared__ int s_tile[GG::NG];
     __shared__ int s_nb[GG::NG][6];
     __shared__ int s_fmask[GG::NG];
+    __shared__ GroupQueue gqs[GG::NG];
     const int gi = threadIdx.x / GG::GT, gt = threadIdx.x % GG::GT, bid = 1 + gi;
     AdjSmem<T, BX, BY, BZ> &sm = sms[gi];
     // faces that never get loaded stay +inf / 0 (z of 2D tiles, far corners)
@@ -347,12 +355,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
         __syncthreads();
         const int n = min(s_n, P.n_tiles);
         if (r > 0) width = adapt_window(width, s_p, n_prev, groups, groups);
+        const int chunk = group_chunk(n, r > 0 ? s_p : 0, r > 0 ? n_prev : 0, groups, GG::GT);
         n_prev = n;
         if (n == 0) break;
         if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); break; }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctl->rcnt[(r + 2) % 3] = 0;
             ctl->rkmin[(r + 2) % 3] = kKeyInf;
+            ctl->rgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
         const OrderCtx ord = order_begin(P.ordered, s_k, width);
@@ -360,53 +370,67 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
         const int *in = (r & 1) ? P.list1 : P.list0;
         int *out = (r & 1) ? P.list0 : P.list1;
         const int next_stamp = r + 2;
-        for (int idx = blockIdx.x * GG::NG + gi; idx < n; idx += groups) {
-            group_sync(bid, GG::GT);
+        // groups take chunks of the list from a shared counter, classify a chunk
+        // with all their threads (deferred entries are listed again on the spot)
+        // and visit the kept tiles one by one
+        GroupQueue &q = gqs[gi];
+        int *grab = &ctl->rgrab[r % 3];
+        for (;;) {
             if (gt == 0) {
-                const int g = __ldcg(in + idx);
-                s_tile[gi] = g;
-#pragma unroll
-                for (int f = 0; f < 6; ++f) s_nb[gi][f] = __ldcg(P.tile_rec + 8 * g + f);
-                s_fmask[gi] = 0;
+                q.n = 0;
+                q.base = atomicAdd(grab, chunk);
             }
             group_sync(bid, GG::GT);
-            const int g = s_tile[gi];
-            if (ord.on) {
-                const unsigned key = __ldg(P.tkey + g);
-                if (!order_visit(ord, key)) {     // deferred: listed again, not visited
-                    if (gt < 32) {
-                        bool want = false;
-                        if (gt == 0) {
-                            want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
-                            deferred++;
-                        }
-                        warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, &ctl->rkmin[nslot], key);
+            const int base = q.base;
+            if (base >= n) break;                          // group-uniform
+            {
+                const int e = base + gt;
+                const bool valid = gt < chunk && e < n;
+                const int g = valid ? __ldcg(in + e) : -1;
+                const unsigned key = valid && ord.on ? __ldg(P.tkey + g) : kKeyInf;
+                const bool defer = valid && ord.on && !order_visit(ord, key);
+                bool want = false;
+                if (defer) {                               // deferred: listed again, not visited
+                    want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
+                    deferred++;
+                }
+                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, ord.on ? &ctl->rkmin[nslot] : nullptr, key);
+                if (valid && !defer) q.tile[atomicAdd(&q.n, 1)] = g;
+            }
+            group_sync(bid, GG::GT);
+            const int qn = q.n;
+            for (int qi = 0; qi < qn; ++qi) {
+                const int g = q.tile[qi];
+                if (gt == 0) {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) s_nb[gi][f] = __ldcg(P.tile_rec + 8 * g + f);
+                    s_fmask[gi] = 0;
+                }
+                group_sync(bid, GG::GT);
+                int nb[6];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
+                unsigned mine;
+                bool changed;
+                const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
+                if (gt == 0) { tiles++; sweeps += s; atomicAdd(&s_visits, 1); }
+#pragma unroll
+                for (int m = 0; m < GG::NPT; ++m)
+                    if (mine >> m & 1) {
+                        const int fb = G::faces_of(gt + GG::GT * m);
+                        if (fb) atomicOr(&s_fmask[gi], fb);
                     }
-                    continue;
+                group_sync(bid, GG::GT);
+                if (gt < 32) {
+                    const int fm = s_fmask[gi];
+                    int cand = -1;
+                    if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
+                    if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+                    const unsigned kc = (ord.on && cand >= 0) ? __ldg(P.tkey + cand) : kKeyInf;
+                    const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+                    warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
                 }
-            }
-            int nb[6];
-#pragma unroll
-            for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
-            unsigned mine;
-            bool changed;
-            const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
-            if (gt == 0) { tiles++; sweeps += s; atomicAdd(&s_visits, 1); }
-#pragma unroll
-            for (int m = 0; m < GG::NPT; ++m)
-                if (mine >> m & 1) {
-                    const int fb = G::faces_of(gt + GG::GT * m);
-                    if (fb) atomicOr(&s_fmask[gi], fb);
-                }
-            group_sync(bid, GG::GT);
-            if (gt < 32) {
-                const int fm = s_fmask[gi];
-                int cand = -1;
-                if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
-                if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
-                const unsigned kc = (ord.on && cand >= 0) ? __ldg(P.tkey + cand) : kKeyInf;
-                const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
-                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
+                group_sync(bid, GG::GT);                   // the visit is done with s_nb, s_fmask and sm
             }
         }
         __syncthreads();
@@ -414,11 +438,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 2) k_adj_persistent(AdjPara
         if (!grid_sync(ctl, target)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters_remedy = r;
-    if (threadIdx.x == 0) {
-        if (tiles) atomicAdd((unsigned long long *)&ctl->tiles_remedy, (unsigned long long)tiles);
-        if (sweeps) atomicAdd((unsigned long long *)&ctl->sweeps, (unsigned long long)sweeps);
-        if (deferred) atomicAdd((unsigned long long *)&ctl->tiles_deferred, (unsigned long long)deferred);
-    }
+    // visits and sweeps are counted by thread 0 of each group, deferrals by the classifying threads
+    if (tiles) atomicAdd((unsigned long long *)&ctl->tiles_remedy, (unsigned long long)tiles);
+    if (sweeps) atomicAdd((unsigned long long *)&ctl->sweeps, (unsigned long long)sweeps);
+    if (deferred) atomicAdd((unsigned long long *)&ctl->tiles_deferred, (unsigned long long)deferred);
 }
 
 // g_out[instance][node] += 2 h tau lambda at non-source nodes with finite phi and tau

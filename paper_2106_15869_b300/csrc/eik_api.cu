@@ -540,7 +540,7 @@ bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout 
 template <class T, int BX, int BY, int BZ>
 int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, const void *phi, const int64_t *src_idx,
                 int64_t n_src, const void *r, void *g, cudaStream_t st, eik_stats *stats) {
-    using GG = GroupGeom<BX, BY, BZ>;
+    using GG = AdjGroupGeom<BX, BY, BZ>;
     AdjParams<T> P;
     P.desc = reinterpret_cast<const InstDesc *>(ws + L.desc);
     P.B = (int)L.desc_host.size();
@@ -594,6 +594,10 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     if (rc) return rc;
     constexpr int CTA = 32 * kWarpsPerCta;
     const size_t dsm = sizeof(AdjSmem<T, BX, BY, BZ>) * GG::NG;
+    // staged blocks of every group of the CTA (above the 48 KiB default for FP64 and 2D tiles)
+    EIK_CUDA(cudaFuncSetAttribute((const void *)k_adj_persistent<T, BX, BY, BZ>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm),
+             "dynamic shared memory attribute");
     int per_sm = 0;
     EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_persistent<T, BX, BY, BZ>, CTA, dsm),
              "occupancy query");

@@ -20,11 +20,11 @@ namespace eik {
 constexpr int kGroupThreads = 256;
 static_assert(kGroupThreads <= 32 * kWarpsPerCta, "a group fits in a CTA");
 
-template <int BX, int BY, int BZ>
+template <int BX, int BY, int BZ, int MaxGT = kGroupThreads>
 struct GroupGeom {
     using G = TileGeom<BX, BY, BZ>;
     static constexpr int CTA = 32 * kWarpsPerCta;
-    static constexpr int GT = G::V >= kGroupThreads ? kGroupThreads : G::V;   // threads per group
+    static constexpr int GT = G::V >= MaxGT ? MaxGT : G::V;   // threads per group
     static constexpr int NG = CTA / GT;                    // groups per CTA
     static constexpr int NPT = G::V / GT;                  // nodes per thread
     static_assert(NG <= kWarpsPerCta && NG <= 8, "one staged block per group");
