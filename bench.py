@@ -44,11 +44,12 @@ FALLBACK_HBM_GBS = 6400.0
 # k_persistent, k_unpack
 LAUNCHES_PER_SOLVE = 7
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_persistent launch,
-# from the ncu capture summarised in profiles/k_persistent_oscillating256.md; reported only
-# while the kernel sources still hash to the captured version (else null).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_persistent launch with
+# the default options, from the ncu capture summarised in profiles/k_persistent_oscillating256.md;
+# reported only for those options and while the kernel sources still hash to the captured
+# version (else null).
 MEASURED_TRAFFIC = {
-    "oscillating_256": {"hash": "5df275c1ac9ad5b3", "bytes": 346479104 + 84680704},
+    "oscillating_256": {"hash": "34ce22a462d4bdd7", "bytes": 347855616 + 84214272},
 }
 
 
@@ -301,7 +302,10 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = measured_peaks()
     achieved = LOOP_BYTES_PER_NODE * n_nodes / (loop_ms / 1e3) / 1e9
     src_hash = kernel_source_hash()
-    traffic = MEASURED_TRAFFIC.get(args.workload)
+    # the captured traffic belongs to the default options only
+    default_opts = (args.method == "ifim" and args.tile == "auto" and args.schedule == "auto"
+                    and args.order == 0.0 and args.converge == "auto")
+    traffic = MEASURED_TRAFFIC.get(args.workload) if default_opts else None
     traffic = traffic["bytes"] if traffic and traffic.get("hash") == src_hash else None
     roofline = {"bound": "hbm", "kernel": "k_persistent (Steps 2-3)", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
