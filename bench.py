@@ -313,6 +313,16 @@ def run_ours(args, ws, rank, local):
                 "loop_ms": loop_ms, "loop_share_of_step": loop_ms / ms_step,
                 "step_achieved_gbs": STEP_BYTES_PER_NODE * n_nodes / (ms_step / 1e3) / 1e9}
     s0 = stats[-1]
+    # work of the loop: in-tile sweeps x nodes per tile (every sweep solves each node of its tile once)
+    if args.tile == "auto":
+        tile_v = 256 if all(i.dims[2] == 1 for i in insts) else 512
+    else:
+        bx, by, bz = (int(v) for v in args.tile.split("x"))
+        tile_v = bx * by * bz
+    solves = s0["sweeps"] * tile_v
+    work = {"local_solves": solves, "local_solves_per_node": solves / n_nodes,
+            "local_solves_per_s": solves / (loop_ms / 1e3), "tile_visits": s0["tiles_update"] + s0["tiles_remedy"],
+            "tile_nodes": tile_v}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -321,7 +331,7 @@ def run_ours(args, ws, rank, local):
                        "converge": args.converge, "method": args.method,
                        "l2": "flushed between steps (256 MiB write outside the per-step events)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "work": work, "e2e": e2e, "clocks": clocks,
             "gpu_launches": LAUNCHES_PER_SOLVE * args.steps,
             "solver_stats": {k: s0[k] for k in ("iters_update", "iters_remedy", "tiles_update",
                                                 "tiles_flagged", "tiles_remedy", "sweeps", "tiles_deferred")},

@@ -160,7 +160,7 @@ __device__ __forceinline__ T local_solve(T ax, T ay, T az, T tau) {
 // FP32 form for the relaxation sweeps, where the latency of one root is on the
 // critical path of the wavefront: the same cascade, but the three candidate
 // roots are formed at once (their square roots overlap) and then selected,
-// and the square root is x * rsqrt(x) (a few ulp; the FP32 solve is judged at
+// and the square root is x * rsqrt(x) (a few ulp; the FP32 solve is held to
 // 1e-4 of max(phi)).  A candidate whose branch is not taken may be NaN or inf
 // (an infinite minimum); it is never selected.
 __device__ __forceinline__ float sqrt_approx(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
