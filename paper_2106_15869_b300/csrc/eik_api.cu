@@ -337,11 +337,18 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     rc = device_info(di);
     if (rc) return rc;
     constexpr int CTA = 32 * kWarpsPerCta;
-    int per_sm = 0;
-    EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<T, BX, BY, BZ>, CTA, 0),
+    // the latency-only persistent kernel for FP32 8x8x8 tiles up to kLatencyTilesPerSM tiles per SM
+    const void *kpers = (const void *)k_persistent<T, BX, BY, BZ, kPersistMixed>;
+    if constexpr (sizeof(T) == 4 && BX * BY * BZ == 512) {
+        if (L.n_tiles <= (long long)kLatencyTilesPerSM * di.sms)
+            kpers = (const void *)k_persistent<T, BX, BY, BZ, kPersistLatency>;
+    }
+    int per_sm = 0, per_sm_pers = 0;
+    EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<T, BX, BY, BZ, kPersistMixed>, CTA, 0),
              "occupancy query");
+    EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pers, kpers, CTA, 0), "occupancy query");
     int sched = o.schedule;
-    if (sched == EIK_SCHED_AUTO) sched = (di.coop && per_sm > 0) ? EIK_SCHED_PERSISTENT : EIK_SCHED_HOSTLOOP;
+    if (sched == EIK_SCHED_AUTO) sched = (di.coop && per_sm_pers > 0) ? EIK_SCHED_PERSISTENT : EIK_SCHED_HOSTLOOP;
 
     bool done = false;
     pe.record(1, st);
@@ -368,13 +375,12 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         done = true;
     }
     if (!done && sched == EIK_SCHED_PERSISTENT) {
-        int grid = per_sm * di.sms;
+        int grid = per_sm_pers * di.sms;
         const int need = (int)((L.n_tiles + kWarpsPerCta - 1) / kWarpsPerCta);
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         void *args[] = {&P};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_persistent<T, BX, BY, BZ>, dim3(grid),
-                                                    dim3(CTA), args, 0, st);
+        cudaError_t e = cudaLaunchCooperativeKernel(kpers, dim3(grid), dim3(CTA), args, 0, st);
         if (e == cudaSuccess) {
             done = true;
         } else if (o.schedule == EIK_SCHED_PERSISTENT) {

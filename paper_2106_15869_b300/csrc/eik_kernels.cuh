@@ -257,6 +257,22 @@ constexpr int min_ctas() {
            : TileGeom<BX, BY, BZ>::NPL <= 8 ? 3 : 2;
 }
 
+// Persistent-kernel variants.  kPersistMixed takes each iteration in the
+// latency mode or the throughput mode by its list size; kPersistLatency takes
+// every iteration in the latency mode.  Without the throughput mode's per-lane
+// node arrays the latter needs fewer registers, so more CTAs (and thread
+// groups) are resident: faster where the lists stay short (bucketed order,
+// up to a few hundred tiles per SM), slower on long lists, where the
+// throughput mode's visits skip unchanged node slots.
+enum : int { kPersistMixed = 0, kPersistLatency = 1 };
+constexpr int kLatencyTilesPerSM = 640;   // the host takes kPersistLatency up to this many tiles per SM
+
+template <class T, int BX, int BY, int BZ, int MODE>
+constexpr int persistent_min_ctas() {
+    return (MODE == kPersistLatency && sizeof(T) == 4 && min_ctas<T, BX, BY, BZ>() < 3) ? 3
+                                                                                        : min_ctas<T, BX, BY, BZ>();
+}
+
 template <class T, int BX, int BY, int BZ>
 struct WarpSmem {
     T phi[kWarpsPerCta][TileGeom<BX, BY, BZ>::S];
@@ -265,8 +281,9 @@ struct WarpSmem {
 // Steps 2 and 3 in one cooperative launch; iterations are separated by the
 // bounded grid barrier.  Every warp reads the same list size after a
 // barrier, so all CTAs leave the loops together.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())) k_persistent(FwdParams<T> P) {
+template <class T, int BX, int BY, int BZ, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX, BY, BZ, MODE>()))
+    k_persistent(FwdParams<T> P) {
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
     __shared__ GroupQueue gqs[GroupGeom<BX, BY, BZ>::NG];
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
             ctl->grab[(it + 2) % 3] = 0;
             ctl->nproc[(it + 2) % 4] = 0;
         }
-        if (n <= kGroupModeFactor * groups)
+        if (MODE == kPersistLatency || n <= kGroupModeFactor * groups)
             update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits, t_upd,
                                              sweeps, deferred);
         else
@@ -348,7 +365,7 @@ neighbour_check:
             ctl->rgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
-        if (n <= kGroupModeFactor * groups)
+        if (MODE == kPersistLatency || n <= kGroupModeFactor * groups)
             remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits, t_rem,
                                              sweeps, deferred);
         else
