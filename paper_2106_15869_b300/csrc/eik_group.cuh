@@ -19,6 +19,9 @@ namespace eik {
 // is 1.3-1.5x faster on 2D grids and equal on 3D; 64 is slower on both.
 constexpr int kGroupThreads = 256;
 static_assert(kGroupThreads <= 32 * kWarpsPerCta, "a group fits in a CTA");
+// groups of the latency-only persistent kernel in iterations with more visits
+// expected than 256-thread groups: twice as many groups of half the size
+constexpr int kSmallGroupThreads = 128;
 
 template <int BX, int BY, int BZ, int MaxGT = kGroupThreads>
 struct GroupGeom {
@@ -54,11 +57,12 @@ __device__ __forceinline__ int group_sync_or(int id, int n, int pred) {
 }
 
 // Stage a tile for the group and relax it; returns the sweep count.
-template <class T, int BX, int BY, int BZ>
+template <class T, int BX, int BY, int BZ, int GTM = kGroupThreads>
 __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const GroupCtl &gc, int g, int gt, int bid,
-                                           T (&v)[GroupGeom<BX, BY, BZ>::NPT], unsigned &mine, bool &first_changed) {
+                                           T (&v)[GroupGeom<BX, BY, BZ, GTM>::NPT], unsigned &mine,
+                                           bool &first_changed) {
     using G = TileGeom<BX, BY, BZ>;
-    using GG = GroupGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ, GTM>;
     T tau[GG::NPT];
     int c[GG::NPT];
     const T *pg = P.phi_t + (size_t)g * G::V;
@@ -145,12 +149,12 @@ __device__ __forceinline__ int group_chunk(int n, int visited_prev, int listed_p
 // order of magnitude), classifies a chunk with all its threads at once (a
 // deferred entry is listed again on the spot), queues the tiles to visit and
 // visits them one by one.  `remedy` selects the Step-3 rules (stamps).
-template <class T, int BX, int BY, int BZ, bool remedy>
+template <class T, int BX, int BY, int BZ, bool remedy, int GTM = kGroupThreads>
 __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int it, int n,
                            unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
                            long long &st_sweeps, long long &st_def) {
     using G = TileGeom<BX, BY, BZ>;
-    using GG = GroupGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ, GTM>;
     Ctl *ctl = P.ctl;
     const int nslot = (it + 1) % 3;
     const int *in = (it & 1) ? P.list1 : P.list0;
@@ -212,7 +216,7 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
             T v[GG::NPT];
             unsigned mine;
             bool changed;
-            const int s = group_visit<T, BX, BY, BZ>(P, sm, gc, g, gt, bid, v, mine, changed);
+            const int s = group_visit<T, BX, BY, BZ, GTM>(P, sm, gc, g, gt, bid, v, mine, changed);
             if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
             if (!remedy) {
                 if (changed && (!P.one_visit || s >= P.max_sweeps)) {
@@ -279,19 +283,19 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
     }
 }
 
-template <class T, int BX, int BY, int BZ>
+template <class T, int BX, int BY, int BZ, int GTM = kGroupThreads>
 __device__ void update_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int it, int n,
                                   unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
                                   long long &st_sweeps, long long &st_def) {
-    group_pass<T, BX, BY, BZ, false>(P, smbase, gcs, gqs, it, n, kmin_cur, width, chunk, s_visits, st_tiles,
+    group_pass<T, BX, BY, BZ, false, GTM>(P, smbase, gcs, gqs, it, n, kmin_cur, width, chunk, s_visits, st_tiles,
                                      st_sweeps, st_def);
 }
 
-template <class T, int BX, int BY, int BZ>
+template <class T, int BX, int BY, int BZ, int GTM = kGroupThreads>
 __device__ void remedy_pass_group(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, GroupQueue *gqs, int r, int n,
                                   unsigned kmin_cur, float width, int chunk, int *s_visits, long long &st_tiles,
                                   long long &st_sweeps, long long &st_def) {
-    group_pass<T, BX, BY, BZ, true>(P, smbase, gcs, gqs, r, n, kmin_cur, width, chunk, s_visits, st_tiles,
+    group_pass<T, BX, BY, BZ, true, GTM>(P, smbase, gcs, gqs, r, n, kmin_cur, width, chunk, s_visits, st_tiles,
                                     st_sweeps, st_def);
 }
 

@@ -284,15 +284,18 @@ struct WarpSmem {
 template <class T, int BX, int BY, int BZ, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX, BY, BZ, MODE>()))
     k_persistent(FwdParams<T> P) {
+    using GGS = GroupGeom<BX, BY, BZ, kSmallGroupThreads>;
+    constexpr int NGMAX = GGS::NG > GroupGeom<BX, BY, BZ>::NG ? GGS::NG : GroupGeom<BX, BY, BZ>::NG;
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
-    __shared__ GroupCtl gcs[GroupGeom<BX, BY, BZ>::NG];
-    __shared__ GroupQueue gqs[GroupGeom<BX, BY, BZ>::NG];
+    __shared__ GroupCtl gcs[NGMAX];
+    __shared__ GroupQueue gqs[NGMAX];
     __shared__ int s_n, s_p, s_visits;
     __shared__ unsigned s_k;
     T *my = sm.phi[warp_in_cta()];
     init_stage<T, BX, BY, BZ>(my);
     if (threadIdx.x == 0) s_visits = 0;
     const int groups = gridDim.x * GroupGeom<BX, BY, BZ>::NG;
+    const int groups_s = gridDim.x * GGS::NG;
     float width = 1.0f;
     int n_prev = 0;
     long long tk = 0;
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
         const unsigned kq = s_k;
         if (it > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
         const int chunk = group_chunk(n, it > 0 ? s_p : 0, it > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
+        const int listed_prev = n_prev;
         n_prev = n;
         if (n == 0) break;
         if (it >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
@@ -322,11 +326,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
             ctl->grab[(it + 2) % 3] = 0;
             ctl->nproc[(it + 2) % 4] = 0;
         }
-        if (MODE == kPersistLatency || n <= kGroupModeFactor * groups)
+        if constexpr (MODE == kPersistLatency) {
+            // more visits expected (the last iteration's, or the list) than groups: smaller groups
+            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (it > 0 ? s_p : n) > groups)
+                update_pass_group<T, BX, BY, BZ, kSmallGroupThreads>(
+                    P, &sm.phi[0][0], gcs, gqs, it, n, kq, width,
+                    group_chunk(n, it > 0 ? s_p : 0, it > 0 ? listed_prev : 0, groups_s, GGS::GT), &s_visits, t_upd,
+                    sweeps, deferred);
+            else
+                update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits,
+                                                 t_upd, sweeps, deferred);
+        } else if (n <= kGroupModeFactor * groups) {
             update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits, t_upd,
                                              sweeps, deferred);
-        else
+        } else {
             update_pass<T, BX, BY, BZ>(P, my, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
+        }
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[it % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) goto done;
@@ -356,6 +371,7 @@ neighbour_check:
         const unsigned kq = s_k;
         if (r > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
         const int chunk = group_chunk(n, r > 0 ? s_p : 0, r > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
+        const int listed_prev = n_prev;
         n_prev = n;
         if (n == 0) break;
         if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
@@ -365,11 +381,21 @@ neighbour_check:
             ctl->rgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
-        if (MODE == kPersistLatency || n <= kGroupModeFactor * groups)
+        if constexpr (MODE == kPersistLatency) {
+            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (r > 0 ? s_p : n) > groups)
+                remedy_pass_group<T, BX, BY, BZ, kSmallGroupThreads>(
+                    P, &sm.phi[0][0], gcs, gqs, r, n, kq, width,
+                    group_chunk(n, r > 0 ? s_p : 0, r > 0 ? listed_prev : 0, groups_s, GGS::GT), &s_visits, t_rem,
+                    sweeps, deferred);
+            else
+                remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits,
+                                                 t_rem, sweeps, deferred);
+        } else if (n <= kGroupModeFactor * groups) {
             remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits, t_rem,
                                              sweeps, deferred);
-        else
+        } else {
             remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
+        }
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
         if (!grid_sync(ctl, target)) goto done;
