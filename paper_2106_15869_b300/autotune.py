@@ -1,8 +1,10 @@
-"""Autotuner for the tile shape and the list order of the solve.
+"""Autotuner for the tile shape, the list order and the schedule of the solve.
 
-The best tile shape (4x4x4, 8x4x4, 8x8x4, 8x8x8; 16x16x1 or 8x8x1 in 2D) and
-list order (bucketed or unordered) depend on the grid size, the batch size and
-the speed field (a strong speed contrast defeats the bucketed order).  tune()
+The best tile shape (4x4x4, 8x4x4, 8x8x4, 8x8x8; 16x16x1 or 8x8x1 in 2D),
+list order (bucketed or unordered) and schedule (the persistent kernel with
+its per-iteration list passes, or the asynchronous work queue) depend on the
+grid size, the batch size and the speed field (a strong speed contrast
+defeats the bucketed order).  tune()
 times each candidate on the caller's own inputs (device time from the
 library's CUDA events, median of a few runs) and caches the winner in a JSON
 file keyed by
@@ -26,8 +28,11 @@ import torch
 
 from . import api
 
-CANDIDATES_3D = [dict(tile=t, order=o) for t in ("8x8x4", "8x4x4", "4x4x4", "8x8x8") for o in (0.0, -1.0)]
-CANDIDATES_2D = [dict(tile=t, order=o) for t in ("16x16x1", "8x8x1") for o in (0.0, -1.0)]
+# persistent schedule with either list order, and the asynchronous queue (which has no order)
+CANDIDATES_3D = ([dict(tile=t, order=o, schedule="persistent") for t in ("8x8x4", "8x4x4", "4x4x4", "8x8x8")
+                  for o in (0.0, -1.0)] + [dict(tile=t, order=-1.0, schedule="async") for t in ("8x8x4", "8x8x8")])
+CANDIDATES_2D = ([dict(tile=t, order=o, schedule="persistent") for t in ("16x16x1", "8x8x1") for o in (0.0, -1.0)]
+                 + [dict(tile="16x16x1", order=-1.0, schedule="async")])
 
 _lock = threading.Lock()
 
@@ -79,7 +84,7 @@ def _time_solve(problems, opts, reps):
 
 
 def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=None, force: bool = False) -> dict:
-    """Options (tile, order) for this problem class, timed on `problems` on a cache miss.
+    """Options (tile, order, schedule) for this problem class, timed on `problems` on a cache miss.
 
     problems: a list of (F, src_idx, h) tuples (one for a single solve) on a CUDA
     device.  Returns a dict usable as keyword arguments of api.solve /
@@ -102,7 +107,7 @@ def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=N
             t = _time_solve(problems, c, reps)
         except api._lib.EikonalError:
             continue
-        timings[f"{c['tile']}/order={c['order']}"] = t
+        timings[f"{c['tile']}/order={c['order']}/{c.get('schedule', 'auto')}"] = t
         if t < best_ms:
             best, best_ms = c, t
     if best is None:

@@ -28,6 +28,7 @@ def test_tune_caches_and_solves(tmp_path):
     F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
     path = str(tmp_path / "tune.json")
     opts = autotune.tune([(F, inst.src_idx, inst.h)], cache_path=path, reps=1)
+    assert opts["schedule"] in ("persistent", "async")
     assert opts["tile"] in ("8x8x4", "8x4x4", "4x4x4", "8x8x8") and len(opts["_ms"]) >= 4
     cached = json.load(open(path))
     assert autotune.problem_key(F) in cached
