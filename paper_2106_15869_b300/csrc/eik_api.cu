@@ -337,12 +337,9 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     rc = device_info(di);
     if (rc) return rc;
     constexpr int CTA = 32 * kWarpsPerCta;
-    // the latency-only persistent kernel for FP32 8x8x8 tiles up to kLatencyTilesPerSM tiles per SM
+    // the latency-only persistent kernel for FP32 8x8x8 tiles, the mixed one otherwise
     const void *kpers = (const void *)k_persistent<T, BX, BY, BZ, kPersistMixed>;
-    if constexpr (sizeof(T) == 4 && BX * BY * BZ == 512) {
-        if (L.n_tiles <= (long long)kLatencyTilesPerSM * di.sms)
-            kpers = (const void *)k_persistent<T, BX, BY, BZ, kPersistLatency>;
-    }
+    if constexpr (sizeof(T) == 4 && BX * BY * BZ == 512) kpers = (const void *)k_persistent<T, BX, BY, BZ, kPersistLatency>;
     int per_sm = 0, per_sm_pers = 0;
     EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<T, BX, BY, BZ, kPersistMixed>, CTA, 0),
              "occupancy query");

@@ -259,13 +259,14 @@ constexpr int min_ctas() {
 
 // Persistent-kernel variants.  kPersistMixed takes each iteration in the
 // latency mode or the throughput mode by its list size; kPersistLatency takes
-// every iteration in the latency mode.  Without the throughput mode's per-lane
-// node arrays the latter needs fewer registers, so more CTAs (and thread
-// groups) are resident: faster where the lists stay short (bucketed order,
-// up to a few hundred tiles per SM), slower on long lists, where the
-// throughput mode's visits skip unchanged node slots.
+// every iteration in the latency mode, with 256-thread groups, or 128-thread
+// groups when more visits are expected than there are 256-thread groups.
+// Without the throughput mode's per-lane node arrays it needs fewer
+// registers, so more CTAs (and thread groups) are resident.  The host takes
+// it for FP32 8x8x8 tiles, where it is faster on every workload measured
+// (256^3 to 512^3 grids, ordered and unordered lists, batches of 16 and 64);
+// on the other tile shapes its higher CTA count spills registers.
 enum : int { kPersistMixed = 0, kPersistLatency = 1 };
-constexpr int kLatencyTilesPerSM = 640;   // the host takes kPersistLatency up to this many tiles per SM
 
 template <class T, int BX, int BY, int BZ, int MODE>
 constexpr int persistent_min_ctas() {
