@@ -103,7 +103,8 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
 
 // workspace regions (byte offsets), all 256-byte aligned
 struct Layout {
-    size_t ctl, desc, tile_fstat, inst_scale, tile_inst, tile_nb, tstate, tstamp, tkey, list0, list1, phi_t, tau_t;
+    size_t ctl, desc, tile_fstat, inst_scale, scale_part, scale_done, tile_inst, tile_nb, tstate, tstamp, tkey, list0,
+        list1, phi_t, tau_t;
     size_t q_data, q_seq, q_state, total;
     long long n_tiles;
     unsigned long long q_slots;
@@ -171,6 +172,8 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     L.ctl = take(sizeof(Ctl));
     L.desc = take(sizeof(InstDesc) * (size_t)B);
     L.inst_scale = take(sizeof(float) * (size_t)B);
+    L.scale_part = take(sizeof(ScalePart) * (size_t)scale_chunks(B) * (size_t)B);
+    L.scale_done = take(sizeof(int) * (size_t)B);
     L.tile_inst = take(4 * (size_t)tiles);
     L.tile_nb = take(4 * 8 * (size_t)tiles);
     L.tile_fstat = take(16 * (size_t)tiles);
@@ -288,6 +291,8 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
     P.tkey = reinterpret_cast<unsigned *>(ws + L.tkey);
     P.inst_scale = reinterpret_cast<float *>(ws + L.inst_scale);
+    P.scale_part = reinterpret_cast<ScalePart *>(ws + L.scale_part);
+    P.scale_done = reinterpret_cast<int *>(ws + L.scale_done);
     P.tile_fstat = reinterpret_cast<float *>(ws + L.tile_fstat);
     P.ordered = o.order > 0.0f ? 1 : 0;
     P.order = o.order;
@@ -309,8 +314,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.src_val = static_cast<const T *>(src_val);
     P.n_src = n_src;
     P.phi_out = static_cast<T *>(phi);
-    constexpr int V = BX * BY * BZ;
-    static_assert(sizeof(Ctl) / sizeof(int) <= V, "control block zeroing needs V >= ints in Ctl");
+    static_assert(sizeof(Ctl) / sizeof(int) <= kInitThreads, "control block zeroing by the threads of one CTA");
 
     PhaseEvents pe;
     int rc = EIK_OK;
@@ -318,11 +322,19 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     pe.record(0, st);
     rc = upload_desc(const_cast<InstDesc *>(P.desc), L.desc_host, st);
     if (rc) return rc;
-    k_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
-    EIK_CUDA(cudaGetLastError(), "k_init launch");
+    {
+        DevInfo dinit;
+        rc = device_info(dinit);
+        if (rc) return rc;
+        const long long ctas = std::min<long long>((L.n_tiles + kInitTiles - 1) / kInitTiles, 16ll * dinit.sms);
+        k_init<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kInitThreads, 0, st>>>(P);
+        EIK_CUDA(cudaGetLastError(), "k_init launch");
+    }
     if (P.ordered) {
-        k_scale<BX, BY, BZ><<<P.B, 256, 0, st>>>(P.desc, reinterpret_cast<const float4 *>(P.tile_fstat), P.inst_scale,
-                                                 P.B, P.order);
+        const int chunks = scale_chunks(P.B);
+        k_scale<BX, BY, BZ><<<(unsigned)((long long)chunks * P.B), kScaleThreads, 0, st>>>(
+            P.desc, reinterpret_cast<const float4 *>(P.tile_fstat), P.inst_scale, P.B, chunks, P.order, P.scale_part,
+            P.scale_done);
         EIK_CUDA(cudaGetLastError(), "k_scale launch");
         k_tile_scale<<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P.tile_nb, P.inst_scale,
                                                                                                (int)L.n_tiles);
@@ -445,7 +457,10 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         EIK_CUDA(cudaStreamSynchronize(st), "stream synchronize");
     }
     pe.record(2, st);
-    k_unpack<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    {
+        const long long ctas = std::min<long long>((L.n_tiles + kUnpackTiles - 1) / kUnpackTiles, 16ll * di.sms);
+        k_unpack<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kUnpackThreads, 0, st>>>(P);
+    }
     EIK_CUDA(cudaGetLastError(), "k_unpack launch");
     pe.record(3, st);
     if (stats) return finish_stats(P.ctl, st, stats, &pe);

@@ -43,6 +43,13 @@ struct InstDesc {
     int64_t aux_off;              // element offset of the adjoint's gradient output
 };
 
+// Partial speed statistics of a slice of an instance's tiles (key-scale reduction).
+struct ScalePart {
+    double sum, cnt;
+    float mn, mx;
+    float pad[2];
+};
+
 struct DescChunk {                // by-value kernel parameter (capture-safe upload)
     InstDesc d[kMaxInstPerLaunch];
     int first, count;
@@ -104,6 +111,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+__device__ __forceinline__ double ld_volatile_d(const double *p) { return *(const volatile double *)p; }
+__device__ __forceinline__ float ld_volatile_f(const float *p) { return *(const volatile float *)p; }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
     unsigned long long v;

@@ -44,6 +44,8 @@ struct FwdParams {
     int *tstamp;
     unsigned *tkey;              // [2][n_tiles] encoded list keys (ordered schedule)
     float *inst_scale;           // [B] 1/delta of each instance (ordered schedule)
+    ScalePart *scale_part;       // [B][scale_chunks(B)] partial speed statistics (k_scale)
+    int *scale_done;             // [B] k_scale CTAs finished per instance
     float *tile_fstat;           // [n_tiles][4] sum, count, min, max of the passable speeds (for delta)
     int ordered;                 // 1 = bucketed order of the lists
     float order;                 // bucket width in tile-crossing times

@@ -52,21 +52,42 @@ __global__ void k_write_desc(InstDesc *desc, DescChunk chunk) {
 // keys over too many buckets; it is left unordered (scale 0).
 constexpr double kOrderContrast = 100.0;
 
+constexpr int kScaleThreads = 256;
+constexpr int kScaleUnroll = 8;      // independent loads in flight per thread
+
+// CTAs per instance of k_scale: many for few (large) instances, one for many
+__host__ __device__ constexpr int scale_chunks(long long B) { return B <= 64 ? 64 : (B <= 4096 ? 8 : 1); }
+
+// `chunks` CTAs per instance each reduce a slice of its per-tile statistics
+// into part[]; the last CTA of the instance to finish (counted in done[],
+// zeroed by k_init) combines the slices and writes the key scale.
 template <int BX, int BY, int BZ>
-__global__ void k_scale(const InstDesc *desc, const float4 *tile_fstat, float *inst_scale, int B, float order) {
-    // one CTA per instance: reduce the per-tile statistics of its tiles
-    const int b = blockIdx.x;
+__global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, const float4 *tile_fstat,
+                                                         float *inst_scale, int B, int chunks, float order,
+                                                         ScalePart *part, int *done) {
+    const int b = blockIdx.x / chunks, c = blockIdx.x % chunks;
     if (b >= B) return;
     const InstDesc &d = desc[b];
     const long long nt = (long long)d.tx * d.ty * d.tz;
+    const long long per = (nt + chunks - 1) / chunks;
+    const long long t_end = min(nt, (c + 1) * per);
     double sum = 0.0, cnt = 0.0;
     float mn = __int_as_float(0x7f800000), mx = 0.0f;
-    for (long long t = threadIdx.x; t < nt; t += blockDim.x) {
-        const float4 s = tile_fstat[d.tile_base + t];
-        sum += s.x; cnt += s.y; mn = fminf(mn, s.z); mx = fmaxf(mx, s.w);
+    for (long long t0 = c * per + threadIdx.x; t0 < t_end; t0 += (long long)kScaleThreads * kScaleUnroll) {
+        float4 v[kScaleUnroll];
+#pragma unroll
+        for (int u = 0; u < kScaleUnroll; ++u) {
+            const long long t = t0 + (long long)u * kScaleThreads;
+            v[u] = t < t_end ? __ldg(tile_fstat + d.tile_base + t) : make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kScaleUnroll; ++u) {
+            sum += v[u].x; cnt += v[u].y; mn = fminf(mn, v[u].z); mx = fmaxf(mx, v[u].w);
+        }
     }
-    __shared__ double s_sum[32], s_cnt[32];
-    __shared__ float s_mn[32], s_mx[32];
+    __shared__ double s_sum[kScaleThreads / 32], s_cnt[kScaleThreads / 32];
+    __shared__ float s_mn[kScaleThreads / 32], s_mx[kScaleThreads / 32];
+    __shared__ int s_last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -77,9 +98,23 @@ __global__ void k_scale(const InstDesc *desc, const float4 *tile_fstat, float *i
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) { s_sum[w] = sum; s_cnt[w] = cnt; s_mn[w] = mn; s_mx[w] = mx; }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-        sum += s_sum[q]; cnt += s_cnt[q]; mn = fminf(mn, s_mn[q]); mx = fmaxf(mx, s_mx[q]);
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kScaleThreads / 32; ++q) {
+            sum += s_sum[q]; cnt += s_cnt[q]; mn = fminf(mn, s_mn[q]); mx = fmaxf(mx, s_mx[q]);
+        }
+        ScalePart &p = part[(size_t)b * chunks + c];
+        p.sum = sum; p.cnt = cnt; p.mn = mn; p.mx = mx;
+        __threadfence();
+        s_last = atomicAdd(done + b, 1) == chunks - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    sum = 0.0; cnt = 0.0; mn = __int_as_float(0x7f800000); mx = 0.0f;
+    for (int q = 0; q < chunks; ++q) {
+        const ScalePart &p = part[(size_t)b * chunks + q];
+        sum += ld_volatile_d(&p.sum); cnt += ld_volatile_d(&p.cnt);
+        mn = fminf(mn, ld_volatile_f(&p.mn)); mx = fmaxf(mx, ld_volatile_f(&p.mx));
     }
     const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
     const double meanF = cnt > 0 ? sum / cnt : 0.0;
@@ -89,73 +124,124 @@ __global__ void k_scale(const InstDesc *desc, const float4 *tile_fstat, float *i
     inst_scale[b] = (float)sc;
 }
 
-// Step 1a: bricked tau = h/F and phi = +inf; per-tile state and neighbour
-// ids; control block.  One CTA of V threads per tile.
+// Step 1a: bricked tau = h/F and phi = +inf; per-tile state, neighbour ids
+// and (ordered schedule) speed statistics; control block.  A CTA takes
+// kInitTiles consecutive tiles at a time: one thread per tile works out its
+// instance and place, then every thread loads its kInitTiles * V /
+// kInitThreads speeds at once (rows of BX nodes of the caller's grid) and
+// writes the bricks (one contiguous block).
+constexpr int kInitThreads = 256;
+constexpr int kInitTiles = 4;
+
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_init(FwdParams<T> P) {
+__global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    __shared__ int s_b;
-    const int g = blockIdx.x;
-    if (threadIdx.x == 0) s_b = find_inst_by_tile(P.desc, P.B, g);
-    __syncthreads();
-    const InstDesc &d = P.desc[s_b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    constexpr int NT = kInitTiles;
+    constexpr int PER = NT * G::V / kInitThreads;
+    static_assert(NT * G::V % kInitThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
+    __shared__ int s_inst[NT], s_lim[NT][3], s_tc[NT][3], s_nx[NT], s_l[NT];
+    __shared__ long long s_fbase[NT], s_plane[NT];
+    __shared__ double s_h[NT];
+    __shared__ float s_acc[NT][4];            // sum, count, min, max of the passable speeds
     const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    T tau = Num<T>::inf();
-    double fsum = 0.0, fcnt = 0.0;
-    if (i < d.nx && j < d.ny && k < d.nz) {
-        const T f = P.F[d.in_off + ((long long)k * d.ny + j) * d.nx + i];
-        if (f > T(0)) { tau = T(d.h) / f; fsum = (double)f; fcnt = 1.0; }
-    }
-    P.tau_t[(size_t)g * G::V + tid] = tau;
-    P.phi_t[(size_t)g * G::V + tid] = Num<T>::inf();
-    if (tid == 0) {
-        P.tile_inst[g] = s_b;
-        P.tstate[g] = kDistant;
-        P.tstamp[g] = 0;
-        P.tkey[g] = kKeyInf;
-        P.tkey[P.n_tiles + g] = kKeyInf;
-    }
-    if (tid < 8) {   // tile record: neighbours, instance, key scale
-        int nb;
-        switch (tid) {
-            case 0: nb = tx > 0 ? g - 1 : -1; break;
-            case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
-            case 2: nb = ty > 0 ? g - d.tx : -1; break;
-            case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
-            case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
-            case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
-            case 6: nb = s_b; break;
-            default: nb = __float_as_int(1.0f); break;   // key scale, set by k_tile_scale
-        }
-        P.tile_nb[8 * g + tid] = nb;
-    }
-    if (P.ordered) {   // per-tile sum, count, min and max of the passable speeds (for the bucket width)
-        __shared__ float s_red[4][32];
-        float fs = (float)fsum, fc = (float)fcnt;
-        float fmn = fcnt > 0 ? fs : __int_as_float(0x7f800000), fmx = fcnt > 0 ? fs : 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fs += __shfl_xor_sync(0xffffffffu, fs, o);
-            fc += __shfl_xor_sync(0xffffffffu, fc, o);
-            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-        }
-        if ((tid & 31) == 0) { s_red[0][tid >> 5] = fs; s_red[1][tid >> 5] = fc; s_red[2][tid >> 5] = fmn; s_red[3][tid >> 5] = fmx; }
-        __syncthreads();
-        if (tid == 0) {
-            float a = 0.f, c = 0.f, mn = __int_as_float(0x7f800000), mx = 0.f;
-            for (int w = 0; w < (G::V + 31) / 32; ++w) {
-                a += s_red[0][w]; c += s_red[1][w]; mn = fminf(mn, s_red[2][w]); mx = fmaxf(mx, s_red[3][w]);
+    const long long total = (long long)P.n_tiles * G::V;
+    for (long long g0 = (long long)blockIdx.x * NT; g0 < P.n_tiles; g0 += (long long)gridDim.x * NT) {
+        if (tid < NT) {
+            const long long g = g0 + tid;
+            int b = 0, lx = 0, ly = 0, lz = 0, nx = 0, l = 0, tx = 0, ty = 0, tz = 0;
+            long long fbase = 0, plane = 0;
+            double h = 0.0;
+            if (g < P.n_tiles) {
+                b = P.B == 1 ? 0 : find_inst_by_tile(P.desc, P.B, g);
+                const InstDesc &d = P.desc[b];
+                l = (int)(g - d.tile_base);                // fewer than 2^31 tiles
+                tx = l % d.tx; ty = (l / d.tx) % d.ty; tz = l / (d.tx * d.ty);
+                lx = min(BX, d.nx - tx * BX); ly = min(BY, d.ny - ty * BY); lz = min(BZ, d.nz - tz * BZ);
+                nx = d.nx;
+                plane = (long long)d.nx * d.ny;
+                fbase = d.in_off + (long long)tz * BZ * plane + (long long)ty * BY * d.nx + (long long)tx * BX;
+                h = d.h;
             }
-            reinterpret_cast<float4 *>(P.tile_fstat)[g] = make_float4(a, c, mn, mx);
+            s_inst[tid] = b; s_l[tid] = l;
+            s_tc[tid][0] = tx; s_tc[tid][1] = ty; s_tc[tid][2] = tz;
+            s_lim[tid][0] = lx; s_lim[tid][1] = ly; s_lim[tid][2] = lz;
+            s_nx[tid] = nx; s_plane[tid] = plane; s_fbase[tid] = fbase; s_h[tid] = h;
+            s_acc[tid][0] = 0.0f; s_acc[tid][1] = 0.0f;
+            s_acc[tid][2] = __int_as_float(0x7f800000); s_acc[tid][3] = 0.0f;
         }
-    }
-    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
-        const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
-        reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+        __syncthreads();
+        T f[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = tid + m * kInitThreads, t = r / G::V, q = r % G::V;
+            const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
+            f[m] = T(0);                                    // outside the grid: tau = +inf
+            if (x < s_lim[t][0] && y < s_lim[t][1] && z < s_lim[t][2])
+                f[m] = P.F[s_fbase[t] + (long long)z * s_plane[t] + (long long)y * s_nx[t] + x];
+        }
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = tid + m * kInitThreads, t = r / G::V;
+            const long long e = g0 * G::V + r;
+            const bool pass = f[m] > T(0);
+            if (e < total) {
+                P.tau_t[e] = pass ? T(s_h[t]) / f[m] : Num<T>::inf();
+                P.phi_t[e] = Num<T>::inf();
+            }
+            if (P.ordered) {   // a warp's 32 nodes lie in one tile
+                float fs = pass ? (float)f[m] : 0.0f, fc = pass ? 1.0f : 0.0f;
+                float fmn = pass ? fs : __int_as_float(0x7f800000), fmx = fs;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fs += __shfl_xor_sync(0xffffffffu, fs, o);
+                    fc += __shfl_xor_sync(0xffffffffu, fc, o);
+                    fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+                    fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+                }
+                if ((tid & 31) == 0) {
+                    atomicAdd(&s_acc[t][0], fs);
+                    atomicAdd(&s_acc[t][1], fc);
+                    atomicMin(reinterpret_cast<int *>(&s_acc[t][2]), __float_as_int(fmn));   // non-negative floats
+                    atomicMax(reinterpret_cast<int *>(&s_acc[t][3]), __float_as_int(fmx));
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < NT && g0 + tid < P.n_tiles) {
+            const long long g = g0 + tid;
+            const int b = s_inst[tid];
+            if (s_l[tid] == 0) P.scale_done[b] = 0;        // k_scale's completion count of this instance
+            P.tile_inst[g] = b;
+            P.tstate[g] = kDistant;
+            P.tstamp[g] = 0;
+            P.tkey[g] = kKeyInf;
+            P.tkey[P.n_tiles + g] = kKeyInf;
+            if (P.ordered)
+                reinterpret_cast<float4 *>(P.tile_fstat)[g] = make_float4(s_acc[tid][0], s_acc[tid][1], s_acc[tid][2], s_acc[tid][3]);
+        }
+        if (tid < 8 * NT && g0 + tid / 8 < P.n_tiles) {   // tile records: neighbours, instance, key scale
+            const int t = tid / 8, k = tid % 8;
+            const int g = (int)(g0 + t);
+            const InstDesc &d = P.desc[s_inst[t]];
+            const int tx = s_tc[t][0], ty = s_tc[t][1], tz = s_tc[t][2];
+            int nb;
+            switch (k) {
+                case 0: nb = tx > 0 ? g - 1 : -1; break;
+                case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
+                case 2: nb = ty > 0 ? g - d.tx : -1; break;
+                case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
+                case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
+                case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
+                case 6: nb = s_inst[t]; break;
+                default: nb = __float_as_int(1.0f); break;   // key scale, set by k_tile_scale
+            }
+            P.tile_nb[8 * (long long)g + k] = nb;
+        }
+        if (g0 == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
+            const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
+            reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+        }
+        __syncthreads();                                       // the tile table is rewritten next
     }
 }
 
@@ -498,19 +584,61 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     flush_stats<T>(P, 0, 0, t, s, d);
 }
 
-// Output: bricked phi -> caller's row-major phi.  One CTA of V threads per tile.
+// Output: bricked phi -> the caller's row-major phi.  A CTA takes
+// kUnpackTiles consecutive bricks at a time (one contiguous block): one thread
+// per brick works out where the brick lies in its instance's grid, then every
+// thread moves kUnpackTiles * V / kUnpackThreads nodes, all loads (coalesced,
+// streaming) issued before the stores (32-byte rows of a tile for BX = 8 FP32).
+constexpr int kUnpackThreads = 256;
+constexpr int kUnpackTiles = 4;
+
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_unpack(FwdParams<T> P) {
+__global__ void __launch_bounds__(kUnpackThreads) k_unpack(FwdParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    const int g = blockIdx.x;
-    const int b = P.tile_inst[g];
-    const InstDesc &d = P.desc[b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
-    const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    if (i < d.nx && j < d.ny && k < d.nz)
-        P.phi_out[d.out_off + ((long long)k * d.ny + j) * d.nx + i] = P.phi_t[(size_t)g * G::V + tid];
+    constexpr int PER = kUnpackTiles * G::V / kUnpackThreads;
+    static_assert(kUnpackTiles * G::V % kUnpackThreads == 0, "whole nodes per thread");
+    __shared__ long long s_base[kUnpackTiles];     // output offset of the brick's node (0, 0, 0)
+    __shared__ int s_lim[kUnpackTiles][3];         // nodes of the brick inside the grid per axis
+    __shared__ int s_nx[kUnpackTiles];
+    __shared__ long long s_plane[kUnpackTiles];
+    for (long long g0 = (long long)blockIdx.x * kUnpackTiles; g0 < P.n_tiles; g0 += (long long)gridDim.x * kUnpackTiles) {
+        if (threadIdx.x < kUnpackTiles) {
+            const long long g = g0 + threadIdx.x;
+            int lx = 0, ly = 0, lz = 0, nx = 0;
+            long long base = 0, plane = 0;
+            if (g < P.n_tiles) {
+                const InstDesc &d = P.desc[P.tile_inst[g]];
+                const long long l = g - d.tile_base;
+                const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+                lx = min(BX, d.nx - tx * BX); ly = min(BY, d.ny - ty * BY); lz = min(BZ, d.nz - tz * BZ);
+                nx = d.nx;
+                plane = (long long)d.nx * d.ny;
+                base = d.out_off + (long long)tz * BZ * plane + (long long)ty * BY * d.nx + (long long)tx * BX;
+            }
+            s_base[threadIdx.x] = base;
+            s_lim[threadIdx.x][0] = lx; s_lim[threadIdx.x][1] = ly; s_lim[threadIdx.x][2] = lz;
+            s_nx[threadIdx.x] = nx;
+            s_plane[threadIdx.x] = plane;
+        }
+        __syncthreads();
+        const long long e0 = g0 * G::V;
+        const long long total = (long long)P.n_tiles * G::V;
+        T val[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const long long e = e0 + threadIdx.x + (long long)m * kUnpackThreads;
+            val[m] = e < total ? __ldcs(P.phi_t + e) : T(0);
+        }
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = threadIdx.x + m * kUnpackThreads;        // node within this CTA's block
+            const int t = r / G::V, q = r % G::V;
+            const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
+            if (x < s_lim[t][0] && y < s_lim[t][1] && z < s_lim[t][2])
+                P.phi_out[s_base[t] + (long long)z * s_plane[t] + (long long)y * s_nx[t] + x] = val[m];
+        }
+        __syncthreads();                                            // the brick table is rewritten next
+    }
 }
 
 }  // namespace eik
