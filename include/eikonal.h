@@ -190,14 +190,18 @@ int eik_solve_batched(int64_t B, const eik_grid *grids, const void *F_packed, co
  *   phi_packed/phi_offsets   device forward solutions, one [nz][ny][nx] block per instance
  *   r_packed                 device dL/dphi, same offsets as phi
  *   g_packed/g_offsets       device output, ACCUMULATED (g += dL/ds); instances may share a
- *                            block (g_offsets equal) to sum their gradients
+ *                            block (g_offsets equal, equal dims) to sum their gradients, in
+ *                            instance order; blocks at different offsets must not overlap
+ *                            (EIK_ERR_ARG otherwise)
  * stats (nullable): tiles_remedy = adjoint tile visits, iters_remedy = iterations.
  * Workspace: eik_adjoint_workspace_size_batched (4 arrays of the precision per node).
  * Options: tile and order as for the solve, but with the adjoint's own defaults
  * (tile 8x8x8 in 3D, order 8: its lists are ordered by a static key, -max phi
  * per tile, so lambda flows from late to early arrivals); method, converge and
  * skip_remedy do not apply.  The result does not depend on tile, order or
- * schedule: the sum in each node has a fixed order.
+ * schedule: the sum in each node has a fixed order, and so has the sum over the
+ * instances that share a gradient block (no atomics), so repeated calls are
+ * bit-identical.
  */
 size_t eik_adjoint_workspace_size_batched(int64_t B, const eik_grid *grids, const eik_options *opt);
 int eik_adjoint_batched(int64_t B, const eik_grid *grids, const void *F_packed, const int64_t *F_offsets,

@@ -51,6 +51,7 @@ struct AdjParams {
     const InstDesc *desc;       // in_off: F offset; out_off: phi and r offset; aux_off: gradient offset
     int B;
     int n_tiles;
+    int n_acc_tiles;            // tiles of the gradient blocks (of their first instances)
     int *tile_rec;              // [n_tiles][8]: neighbours, instance, unused
     int *tstamp;
     int *list0, *list1;
@@ -85,66 +86,94 @@ struct AdjSmem {
     T lam[TileGeom<BX, BY, BZ>::S];
 };
 
-// Step 0: bricks of tau, phi, r; lambda = 0; tile records; control block.
+// Step 0: bricks of tau, phi, r; lambda = 0; tile records (slot 7: the largest
+// finite phi of the tile, for the list key); control block.  tstamp marks the
+// tiles that seed the first list: those holding a node with r != 0 and finite
+// phi (a tile whose only such nodes are sources gets one visit that changes
+// nothing).  A CTA takes kSpan consecutive tiles at a time, every thread
+// loading its nodes of the three input arrays at once.
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_adj_init(AdjParams<T> P) {
+__global__ void __launch_bounds__(kSpanThreads) k_adj_init(AdjParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    __shared__ int s_b;
-    const int g = blockIdx.x;
-    if (threadIdx.x == 0) s_b = find_inst_by_tile(P.desc, P.B, g);
-    __syncthreads();
-    const InstDesc &d = P.desc[s_b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
+    constexpr int PER = kSpan * G::V / kSpanThreads;
+    static_assert(kSpan * G::V % kSpanThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
+    __shared__ TileSpan<BX, BY, BZ> sp;
+    __shared__ unsigned s_mx[kSpan];           // largest finite phi, encoded (key_enc is monotone)
+    __shared__ int s_seed[kSpan];
     const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    T tau = Num<T>::inf(), phi = Num<T>::inf(), r = T(0);
-    if (i < d.nx && j < d.ny && k < d.nz) {
-        const long long p = ((long long)k * d.ny + j) * d.nx + i;
-        const T f = P.F[d.in_off + p];
-        if (f > T(0)) tau = T(d.h) / f;
-        phi = P.phi_in[d.out_off + p];
-        r = P.r_in[d.out_off + p];
-        if (!(phi < Num<T>::inf())) r = T(0);      // an unreachable receiver has no gradient
-    }
-    const size_t q = (size_t)g * G::V + tid;
-    P.tau_t[q] = tau;
-    P.phi_t[q] = phi;
-    P.lam_t[q] = T(0);
-    P.r_t[q] = r;
-    if (tid == 0) P.tstamp[g] = 0;
-    // largest finite phi of the tile (key of the ordered lists), block-reduced
-    __shared__ float s_mx[32];
-    float mx = phi < Num<T>::inf() ? (float)phi : -__int_as_float(0x7f800000);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0) s_mx[tid >> 5] = mx;
-    __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < (G::V + 31) / 32; ++w) mx = fmaxf(mx, s_mx[w]);
-        P.tile_rec[8 * g + 7] = __float_as_int(mx);
-    }
-    if (tid < 8) {
-        int nb;
-        switch (tid) {
-            case 0: nb = tx > 0 ? g - 1 : -1; break;
-            case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
-            case 2: nb = ty > 0 ? g - d.tx : -1; break;
-            case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
-            case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
-            case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
-            case 6: nb = s_b; break;
-            default: nb = 0; break;   // slot 7 (max phi) is written above
+    const long long total = (long long)P.n_tiles * G::V;
+    for (long long g0 = (long long)blockIdx.x * kSpan; g0 < P.n_tiles; g0 += (long long)gridDim.x * kSpan) {
+        if (tid < kSpan) {
+            sp.fill(P.desc, P.B, P.n_tiles, g0, tid);
+            s_mx[tid] = key_enc(-__int_as_float(0x7f800000));
+            s_seed[tid] = 0;
         }
-        if (tid < 7) P.tile_rec[8 * g + tid] = nb;
-    }
-    if (g == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
-        const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
-        reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+        __syncthreads();
+        T f[PER], ph[PER], rr[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = tid + m * kSpanThreads, t = r / G::V, q = r % G::V;
+            const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
+            f[m] = T(0); ph[m] = Num<T>::inf(); rr[m] = T(0);
+            if (sp.inside(t, x, y, z)) {
+                const InstDesc &d = P.desc[sp.inst[t]];
+                const long long p = sp.at(t, x, y, z);
+                f[m] = P.F[d.in_off + p];
+                ph[m] = P.phi_in[d.out_off + p];
+                rr[m] = P.r_in[d.out_off + p];
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = tid + m * kSpanThreads, t = r / G::V;
+            const long long e = g0 * G::V + r;
+            const bool fin = ph[m] < Num<T>::inf();
+            if (!fin) rr[m] = T(0);                                    // an unreachable receiver has no gradient
+            if (e < total) {
+                P.tau_t[e] = f[m] > T(0) ? T(P.desc[sp.inst[t]].h) / f[m] : Num<T>::inf();
+                P.phi_t[e] = ph[m];
+                P.lam_t[e] = T(0);
+                P.r_t[e] = rr[m];
+            }
+            // a warp's 32 nodes lie in one tile
+            const unsigned k = __reduce_max_sync(0xffffffffu, fin ? key_enc((float)ph[m]) : key_enc(-__int_as_float(0x7f800000)));
+            const bool any = __any_sync(0xffffffffu, rr[m] != T(0));
+            if ((tid & 31) == 0) {
+                atomicMax(&s_mx[t], k);
+                if (any) s_seed[t] = 1;
+            }
+        }
+        __syncthreads();
+        if (tid < kSpan && g0 + tid < P.n_tiles) {
+            const long long g = g0 + tid;
+            P.tile_rec[8 * g + 7] = __float_as_int(key_dec(s_mx[tid]));
+            P.tstamp[g] = s_seed[tid];
+        }
+        if (tid < 8 * kSpan && tid % 8 < 7 && g0 + tid / 8 < P.n_tiles) {   // neighbours and instance
+            const int t = tid / 8, k = tid % 8;
+            const int g = (int)(g0 + t);
+            const InstDesc &d = P.desc[sp.inst[t]];
+            const int tx = sp.tc[t][0], ty = sp.tc[t][1], tz = sp.tc[t][2];
+            int nb;
+            switch (k) {
+                case 0: nb = tx > 0 ? g - 1 : -1; break;
+                case 1: nb = tx + 1 < d.tx ? g + 1 : -1; break;
+                case 2: nb = ty > 0 ? g - d.tx : -1; break;
+                case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
+                case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
+                case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
+                default: nb = sp.inst[t]; break;
+            }
+            P.tile_rec[8 * (long long)g + k] = nb;
+        }
+        if (g0 == 0 && tid < (int)(sizeof(Ctl) / sizeof(int))) {
+            const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
+            reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
+        }
+        __syncthreads();                                       // the span is refilled next
     }
 }
 
-// 1/delta per instance: delta = order * max(phi) / (tiles along x + y + z); one CTA per instance.
 template <class T>
 __global__ void k_adj_scale(AdjParams<T> P) {
     const int b = blockIdx.x;
@@ -165,13 +194,21 @@ __global__ void k_adj_scale(AdjParams<T> P) {
     P.inst_scale[b] = (mx > 0.0f && mx < __int_as_float(0x7f800000)) ? hops / (P.order * mx) : 0.0f;
 }
 
-// static key of every tile: -max(phi) / delta (larger phi first)
+// List keys (ordered lists) and the first list: the tiles k_adj_init marked.
 template <class T>
-__global__ void k_adj_keys(AdjParams<T> P) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.n_tiles; g += gridDim.x * blockDim.x) {
-        const float mx = __int_as_float(P.tile_rec[8 * g + 7]);
-        const float sc = P.inst_scale[P.tile_rec[8 * g + 6]];
-        P.tkey[g] = (mx > -__int_as_float(0x7f800000)) ? scaled_key(-mx, sc) : key_enc(0.0f);
+__global__ void k_adj_list(AdjParams<T> P) {
+    for (int g0 = blockIdx.x * blockDim.x; g0 < P.n_tiles; g0 += gridDim.x * blockDim.x) {   // uniform per warp
+        const int g = g0 + (int)threadIdx.x;
+        const bool valid = g < P.n_tiles;
+        unsigned key = kKeyInf;
+        if (valid && P.ordered) {
+            const float mx = __int_as_float(P.tile_rec[8 * g + 7]);
+            const float sc = P.inst_scale[P.tile_rec[8 * g + 6]];
+            key = (mx > -__int_as_float(0x7f800000)) ? scaled_key(-mx, sc) : key_enc(0.0f);
+            P.tkey[g] = key;
+        }
+        const bool seed = valid && P.tstamp[g] == 1;
+        warp_push(P.ctl, &P.ctl->rcnt[0], P.list0, P.n_tiles, seed, g, P.ordered ? &P.ctl->rkmin[0] : nullptr, key);
     }
 }
 
@@ -191,22 +228,6 @@ __global__ void k_adj_sources(AdjParams<T> P) {
     const int g = (int)(d.tile_base + ((long long)(k / BZ) * d.ty + (j / BY)) * d.tx + (i / BX));
     const int loc = ((k % BZ) * BY + (j % BY)) * BX + (i % BX);
     P.tau_t[(size_t)g * G::V + loc] = T(-1);
-}
-
-// The initial list: tiles holding a non-source node with r != 0.
-template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_adj_seed(AdjParams<T> P) {
-    using G = TileGeom<BX, BY, BZ>;
-    const int g = blockIdx.x;
-    const size_t q = (size_t)g * G::V + threadIdx.x;
-    const int want = (P.r_t[q] != T(0) && !(P.tau_t[q] < T(0))) ? 1 : 0;
-    if (__syncthreads_or(want) && threadIdx.x == 0) {
-        P.tstamp[g] = 1;
-        if (P.ordered) atomicMin(&P.ctl->rkmin[0], P.tkey[g]);
-        const int pos = atomicAdd(&P.ctl->rcnt[0], 1);
-        if (pos < P.n_tiles) P.list0[pos] = g;
-        else atomicOr(&P.ctl->flags, kFlagOverflow);
-    }
 }
 
 // One visit of tile g by a group of GT threads (one or two nodes each).
@@ -446,23 +467,66 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
     if (deferred) atomicAdd((unsigned long long *)&ctl->tiles_deferred, (unsigned long long)deferred);
 }
 
-// g_out[instance][node] += 2 h tau lambda at non-source nodes with finite phi and tau
-// (atomic: instances may share one gradient array).
+// g_out[block][node] += sum over the instances b writing that gradient block,
+// in instance order, of 2 h tau_b lambda_b, at non-source nodes with finite
+// phi and tau (blocks are equal or disjoint, so one thread owns each node: the
+// sum has a fixed order and no atomics).  A CTA takes kSpan consecutive tiles
+// of the blocks (of their first instances) at a time; every thread loads its
+// nodes of each instance at once.
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX *BY *BZ) k_adj_output(AdjParams<T> P) {
+__global__ void __launch_bounds__(kSpanThreads) k_adj_output(AdjParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    const int g = blockIdx.x;
-    const int b = P.tile_rec[8 * g + 6];
-    const InstDesc &d = P.desc[b];
-    const long long l = g - d.tile_base;
-    const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
-    const int tid = threadIdx.x;
-    const int i = tx * BX + tid % BX, j = ty * BY + (tid / BX) % BY, k = tz * BZ + tid / (BX * BY);
-    if (i >= d.nx || j >= d.ny || k >= d.nz) return;
-    const size_t q = (size_t)g * G::V + tid;
-    const T lam = P.lam_t[q], tau = P.tau_t[q], phi = P.phi_t[q];
-    if (lam == T(0) || tau < T(0) || !(tau < Num<T>::inf()) || !(phi < Num<T>::inf())) return;
-    atomicAdd(P.g_out + d.aux_off + ((long long)k * d.ny + j) * d.nx + i, T(2) * T(d.h) * tau * lam);
+    constexpr int PER = kSpan * G::V / kSpanThreads;
+    __shared__ TileSpan<BX, BY, BZ> sp;
+    __shared__ int s_cur[kSpan];                 // instance of each tile's chain being added (-1: done)
+    for (long long a0 = (long long)blockIdx.x * kSpan; a0 < P.n_acc_tiles; a0 += (long long)gridDim.x * kSpan) {
+        if (threadIdx.x < kSpan) {
+            sp.fill(P.desc, P.B, P.n_acc_tiles, a0, threadIdx.x, true);
+            s_cur[threadIdx.x] = a0 + threadIdx.x < P.n_acc_tiles ? sp.inst[threadIdx.x] : -1;
+        }
+        __syncthreads();
+        T sum[PER];
+        bool any[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) { sum[m] = T(0); any[m] = false; }
+        for (;;) {
+            bool live = false;
+#pragma unroll
+            for (int t = 0; t < kSpan; ++t) live |= s_cur[t] >= 0;
+            if (!live) break;                                       // uniform: every thread read the same s_cur
+            T lam[PER], tau[PER], phi[PER], h2[PER];
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int r = threadIdx.x + m * kSpanThreads, t = r / G::V, q = r % G::V;
+                const int b = s_cur[t];
+                lam[m] = T(0); tau[m] = T(-1); phi[m] = Num<T>::inf(); h2[m] = T(0);
+                if (b < 0) continue;
+                const long long e = (P.desc[b].tile_base + sp.l[t]) * G::V + q;
+                lam[m] = __ldcs(P.lam_t + e);
+                tau[m] = __ldcs(P.tau_t + e);
+                phi[m] = __ldcs(P.phi_t + e);
+                h2[m] = T(2) * T(P.desc[b].h);
+            }
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                if (lam[m] == T(0) || tau[m] < T(0) || !(tau[m] < Num<T>::inf()) || !(phi[m] < Num<T>::inf())) continue;
+                sum[m] += h2[m] * tau[m] * lam[m];
+                any[m] = true;
+            }
+            __syncthreads();                                        // s_cur read by all
+            if (threadIdx.x < kSpan && s_cur[threadIdx.x] >= 0) s_cur[threadIdx.x] = P.desc[s_cur[threadIdx.x]].acc_next;
+            __syncthreads();
+        }
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int r = threadIdx.x + m * kSpanThreads, t = r / G::V, q = r % G::V;
+            const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
+            if (!any[m] || !sp.inside(t, x, y, z)) continue;
+            T *o = P.g_out + P.desc[sp.inst[t]].aux_off + sp.at(t, x, y, z);
+            *o += sum[m];
+        }
+        __syncthreads();                                            // the span is refilled next
+    }
 }
 
 }  // namespace eik

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -158,6 +159,8 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
         d.ty = (int)((g.ny + ts.by - 1) / ts.by);
         d.tz = (int)((g.nz + ts.bz - 1) / ts.bz);
         d.tile_base = tiles;
+        d.acc_base = tiles;
+        d.acc_next = -1;
         d.h = g.h;
         tiles += (long long)d.tx * d.ty * d.tz;
         if (tiles >= (1ll << 31) - 1) {
@@ -314,7 +317,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.src_val = static_cast<const T *>(src_val);
     P.n_src = n_src;
     P.phi_out = static_cast<T *>(phi);
-    static_assert(sizeof(Ctl) / sizeof(int) <= kInitThreads, "control block zeroing by the threads of one CTA");
+    static_assert(sizeof(Ctl) / sizeof(int) <= kSpanThreads, "control block zeroing by the threads of one CTA");
 
     PhaseEvents pe;
     int rc = EIK_OK;
@@ -326,8 +329,8 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         DevInfo dinit;
         rc = device_info(dinit);
         if (rc) return rc;
-        const long long ctas = std::min<long long>((L.n_tiles + kInitTiles - 1) / kInitTiles, 16ll * dinit.sms);
-        k_init<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kInitThreads, 0, st>>>(P);
+        const long long ctas = std::min<long long>((L.n_tiles + kSpan - 1) / kSpan, 16ll * dinit.sms);
+        k_init<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kSpanThreads, 0, st>>>(P);
         EIK_CUDA(cudaGetLastError(), "k_init launch");
     }
     if (P.ordered) {
@@ -458,8 +461,8 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     }
     pe.record(2, st);
     {
-        const long long ctas = std::min<long long>((L.n_tiles + kUnpackTiles - 1) / kUnpackTiles, 16ll * di.sms);
-        k_unpack<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kUnpackThreads, 0, st>>>(P);
+        const long long ctas = std::min<long long>((L.n_tiles + kSpan - 1) / kSpan, 16ll * di.sms);
+        k_unpack<T, BX, BY, BZ><<<(unsigned)std::max<long long>(ctas, 1), kSpanThreads, 0, st>>>(P);
     }
     EIK_CUDA(cudaGetLastError(), "k_unpack launch");
     pe.record(3, st);
@@ -521,6 +524,7 @@ int solve_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F
 struct AdjLayout {
     size_t ctl, desc, inst_scale, tile_rec, tstamp, tkey, list0, list1, phi_t, tau_t, lam_t, r_t, total;
     long long n_tiles;
+    long long n_acc_tiles;        // tiles of the distinct gradient blocks
     std::vector<InstDesc> desc_host;
 };
 
@@ -536,6 +540,7 @@ bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout 
     const long long V = (long long)ts.bx * ts.by * ts.bz;
     L.desc_host = fl.desc_host;
     L.n_tiles = fl.n_tiles;
+    L.n_acc_tiles = fl.n_tiles;   // every instance its own block until chain_gradient_blocks
     const long long tiles = fl.n_tiles;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o2 = off; off = align_up(off + bytes, 256); return o2; };
@@ -555,6 +560,38 @@ bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout 
     return true;
 }
 
+// Instances with equal gradient offsets sum into one block: chain them in
+// instance order (acc_next) and number the tiles of each block's first
+// instance (acc_base, monotone over all instances).  Blocks must have equal
+// dims and must not overlap one another, so that one thread owns each output
+// node.
+bool chain_gradient_blocks(AdjLayout &L) {
+    std::map<int64_t, int> first, last;     // gradient offset -> first / last instance of its chain
+    std::vector<std::pair<int64_t, int64_t>> spans;
+    long long acc = 0;
+    for (size_t b = 0; b < L.desc_host.size(); ++b) {
+        InstDesc &d = L.desc_host[b];
+        d.acc_next = -1;
+        d.acc_base = acc;
+        auto it = first.find(d.aux_off);
+        if (it == first.end()) {
+            first[d.aux_off] = last[d.aux_off] = (int)b;
+            acc += (long long)d.tx * d.ty * d.tz;
+            spans.push_back({d.aux_off, d.aux_off + (int64_t)d.nx * d.ny * d.nz});
+            continue;
+        }
+        const InstDesc &f = L.desc_host[(size_t)it->second];
+        if (f.nx != d.nx || f.ny != d.ny || f.nz != d.nz) return false;
+        L.desc_host[(size_t)last[d.aux_off]].acc_next = (int)b;
+        last[d.aux_off] = (int)b;
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t q = 1; q < spans.size(); ++q)
+        if (spans[q].first < spans[q - 1].second) return false;
+    L.n_acc_tiles = acc;
+    return true;
+}
+
 template <class T, int BX, int BY, int BZ>
 int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, const void *phi, const int64_t *src_idx,
                 int64_t n_src, const void *r, void *g, cudaStream_t st, eik_stats *stats) {
@@ -563,6 +600,7 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     P.desc = reinterpret_cast<const InstDesc *>(ws + L.desc);
     P.B = (int)L.desc_host.size();
     P.n_tiles = (int)L.n_tiles;
+    P.n_acc_tiles = (int)L.n_acc_tiles;
     P.tile_rec = reinterpret_cast<int *>(ws + L.tile_rec);
     P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
@@ -586,14 +624,18 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     P.inst_scale = reinterpret_cast<float *>(ws + L.inst_scale);
     P.ordered = o.order > 0.0f ? 1 : 0;
     P.order = o.order;
-    constexpr int V = BX * BY * BZ;
     PhaseEvents pe;
     int rc = EIK_OK;
     if (stats && (rc = pe.create())) return rc;
     pe.record(0, st);
     rc = upload_desc(const_cast<InstDesc *>(P.desc), L.desc_host, st);
     if (rc) return rc;
-    k_adj_init<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    DevInfo di;
+    rc = device_info(di);
+    if (rc) return rc;
+    const unsigned span_ctas =
+        (unsigned)std::max<long long>(1, std::min<long long>((L.n_tiles + kSpan - 1) / kSpan, 16ll * di.sms));
+    k_adj_init<T, BX, BY, BZ><<<span_ctas, kSpanThreads, 0, st>>>(P);
     EIK_CUDA(cudaGetLastError(), "k_adj_init launch");
     if (n_src > 0) {
         k_adj_sources<T, BX, BY, BZ><<<(unsigned)((n_src + 255) / 256), 256, 0, st>>>(P);
@@ -602,14 +644,9 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     if (P.ordered) {
         k_adj_scale<T><<<P.B, 256, 0, st>>>(P);
         EIK_CUDA(cudaGetLastError(), "k_adj_scale launch");
-        k_adj_keys<T><<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P);
-        EIK_CUDA(cudaGetLastError(), "k_adj_keys launch");
     }
-    k_adj_seed<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
-    EIK_CUDA(cudaGetLastError(), "k_adj_seed launch");
-    DevInfo di;
-    rc = device_info(di);
-    if (rc) return rc;
+    k_adj_list<T><<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P);
+    EIK_CUDA(cudaGetLastError(), "k_adj_list launch");
     constexpr int CTA = 32 * kWarpsPerCta;
     const size_t dsm = sizeof(AdjSmem<T, BX, BY, BZ>) * GG::NG;
     // staged blocks of every group of the CTA (above the 48 KiB default for FP64 and 2D tiles)
@@ -630,7 +667,9 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
                                          dsm, st),
              "cooperative launch");
     pe.record(2, st);
-    k_adj_output<T, BX, BY, BZ><<<(unsigned)L.n_tiles, V, 0, st>>>(P);
+    const unsigned acc_ctas =
+        (unsigned)std::max<long long>(1, std::min<long long>((L.n_acc_tiles + kSpan - 1) / kSpan, 16ll * di.sms));
+    k_adj_output<T, BX, BY, BZ><<<acc_ctas, kSpanThreads, 0, st>>>(P);
     EIK_CUDA(cudaGetLastError(), "k_adj_output launch");
     pe.record(3, st);
     if (stats) return finish_stats(P.ctl, st, stats, &pe);
@@ -671,6 +710,7 @@ int adjoint_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t 
         d.src_begin = src_offsets[b];
         d.src_end = src_offsets[b + 1];
     }
+    if (!chain_gradient_blocks(L)) return fail(EIK_ERR_ARG, "gradient blocks must be equal (same offset and dims) or disjoint");
     const int64_t n_src = src_offsets[B];
     if (n_src > 0 && !src_idx) return fail(EIK_ERR_ARG, "src_idx must be non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -33,7 +33,8 @@ constexpr int kFlagOverflow = 8;     // a list push beyond capacity (internal er
 enum TileState : int { kDistant = 0, kActive = 1, kSource = 2 };
 
 struct InstDesc {
-    int32_t nx, ny, nz, pad0;
+    int32_t nx, ny, nz;
+    int32_t acc_next;             // adjoint: next instance summing into the same gradient block (-1: none)
     int32_t tx, ty, tz, pad1;     // tiles per axis
     int64_t tile_base;            // first global tile id of this instance
     int64_t in_off;               // element offset of F (and of r in the adjoint)
@@ -41,6 +42,7 @@ struct InstDesc {
     int64_t src_begin, src_end;   // entries of the packed source arrays
     double h;
     int64_t aux_off;              // element offset of the adjoint's gradient output
+    int64_t acc_base;             // adjoint: tiles of the gradient blocks' first instances before this one
 };
 
 // Partial speed statistics of a slice of an instance's tiles (key-scale reduction).
@@ -302,6 +304,18 @@ __device__ __forceinline__ int find_inst_by_tile(const InstDesc *desc, int B, lo
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (desc[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// binary search over the adjoint's gradient blocks: the last instance with
+// acc_base <= a, which is the first instance of the block holding tile a of
+// the blocks' tile space (acc_base grows only across first instances).
+__device__ __forceinline__ int find_inst_by_acc(const InstDesc *desc, int B, long long a) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].acc_base <= a) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

@@ -124,48 +124,59 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, c
     inst_scale[b] = (float)sc;
 }
 
-// Step 1a: bricked tau = h/F and phi = +inf; per-tile state, neighbour ids
-// and (ordered schedule) speed statistics; control block.  A CTA takes
-// kInitTiles consecutive tiles at a time: one thread per tile works out its
-// instance and place, then every thread loads its kInitTiles * V /
-// kInitThreads speeds at once (rows of BX nodes of the caller's grid) and
-// writes the bricks (one contiguous block).
-constexpr int kInitThreads = 256;
-constexpr int kInitTiles = 4;
+// Geometry of kSpan consecutive tiles for the streaming kernels (layout
+// conversion in and out of the bricks): thread t < kSpan of a CTA fills entry
+// t; every thread then maps its nodes with inside() / at().
+constexpr int kSpan = 4;
+constexpr int kSpanThreads = 256;
 
+template <int BX, int BY, int BZ>
+struct TileSpan {
+    int inst[kSpan], l[kSpan], tc[kSpan][3], lim[kSpan][3], nx[kSpan];
+    long long corner[kSpan], plane[kSpan];   // node (0, 0, 0) of the tile within its instance's grid
+    // acc: g counts the tiles of the adjoint's gradient blocks (acc_base) instead of all tiles
+    __device__ void fill(const InstDesc *desc, int B, long long n_tiles, long long g0, int t, bool acc = false) {
+        const long long g = g0 + t;
+        int b = 0, ll = 0, tx = 0, ty = 0, tz = 0, lx = 0, ly = 0, lz = 0, nxx = 0;
+        long long c = 0, pl = 0;
+        if (g < n_tiles) {
+            b = B == 1 ? 0 : acc ? find_inst_by_acc(desc, B, g) : find_inst_by_tile(desc, B, g);
+            const InstDesc &d = desc[b];
+            ll = (int)(g - (acc ? d.acc_base : d.tile_base));   // fewer than 2^31 tiles
+            tx = ll % d.tx; ty = (ll / d.tx) % d.ty; tz = ll / (d.tx * d.ty);
+            lx = min(BX, d.nx - tx * BX); ly = min(BY, d.ny - ty * BY); lz = min(BZ, d.nz - tz * BZ);
+            nxx = d.nx;
+            pl = (long long)d.nx * d.ny;
+            c = (long long)tz * BZ * pl + (long long)ty * BY * d.nx + (long long)tx * BX;
+        }
+        inst[t] = b; l[t] = ll;
+        tc[t][0] = tx; tc[t][1] = ty; tc[t][2] = tz;
+        lim[t][0] = lx; lim[t][1] = ly; lim[t][2] = lz;
+        nx[t] = nxx; plane[t] = pl; corner[t] = c;
+    }
+    __device__ bool inside(int t, int x, int y, int z) const { return x < lim[t][0] && y < lim[t][1] && z < lim[t][2]; }
+    __device__ long long at(int t, int x, int y, int z) const {
+        return corner[t] + (long long)z * plane[t] + (long long)y * nx[t] + x;
+    }
+};
+
+// Step 1a: bricked tau = h/F and phi = +inf; per-tile state, neighbour ids
+// and (ordered schedule) speed statistics; control block.  A CTA takes kSpan
+// consecutive tiles at a time: every thread loads its kSpan * V /
+// kSpanThreads speeds at once (rows of BX nodes of the caller's grid), then
+// writes the bricks (one contiguous block).
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
+__global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    constexpr int NT = kInitTiles;
-    constexpr int PER = NT * G::V / kInitThreads;
-    static_assert(NT * G::V % kInitThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
-    __shared__ int s_inst[NT], s_lim[NT][3], s_tc[NT][3], s_nx[NT], s_l[NT];
-    __shared__ long long s_fbase[NT], s_plane[NT];
-    __shared__ double s_h[NT];
-    __shared__ float s_acc[NT][4];            // sum, count, min, max of the passable speeds
+    constexpr int PER = kSpan * G::V / kSpanThreads;
+    static_assert(kSpan * G::V % kSpanThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
+    __shared__ TileSpan<BX, BY, BZ> sp;
+    __shared__ float s_acc[kSpan][4];          // sum, count, min, max of the passable speeds
     const int tid = threadIdx.x;
     const long long total = (long long)P.n_tiles * G::V;
-    for (long long g0 = (long long)blockIdx.x * NT; g0 < P.n_tiles; g0 += (long long)gridDim.x * NT) {
-        if (tid < NT) {
-            const long long g = g0 + tid;
-            int b = 0, lx = 0, ly = 0, lz = 0, nx = 0, l = 0, tx = 0, ty = 0, tz = 0;
-            long long fbase = 0, plane = 0;
-            double h = 0.0;
-            if (g < P.n_tiles) {
-                b = P.B == 1 ? 0 : find_inst_by_tile(P.desc, P.B, g);
-                const InstDesc &d = P.desc[b];
-                l = (int)(g - d.tile_base);                // fewer than 2^31 tiles
-                tx = l % d.tx; ty = (l / d.tx) % d.ty; tz = l / (d.tx * d.ty);
-                lx = min(BX, d.nx - tx * BX); ly = min(BY, d.ny - ty * BY); lz = min(BZ, d.nz - tz * BZ);
-                nx = d.nx;
-                plane = (long long)d.nx * d.ny;
-                fbase = d.in_off + (long long)tz * BZ * plane + (long long)ty * BY * d.nx + (long long)tx * BX;
-                h = d.h;
-            }
-            s_inst[tid] = b; s_l[tid] = l;
-            s_tc[tid][0] = tx; s_tc[tid][1] = ty; s_tc[tid][2] = tz;
-            s_lim[tid][0] = lx; s_lim[tid][1] = ly; s_lim[tid][2] = lz;
-            s_nx[tid] = nx; s_plane[tid] = plane; s_fbase[tid] = fbase; s_h[tid] = h;
+    for (long long g0 = (long long)blockIdx.x * kSpan; g0 < P.n_tiles; g0 += (long long)gridDim.x * kSpan) {
+        if (tid < kSpan) {
+            sp.fill(P.desc, P.B, P.n_tiles, g0, tid);
             s_acc[tid][0] = 0.0f; s_acc[tid][1] = 0.0f;
             s_acc[tid][2] = __int_as_float(0x7f800000); s_acc[tid][3] = 0.0f;
         }
@@ -173,19 +184,18 @@ __global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
         T f[PER];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const int r = tid + m * kInitThreads, t = r / G::V, q = r % G::V;
+            const int r = tid + m * kSpanThreads, t = r / G::V, q = r % G::V;
             const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
             f[m] = T(0);                                    // outside the grid: tau = +inf
-            if (x < s_lim[t][0] && y < s_lim[t][1] && z < s_lim[t][2])
-                f[m] = P.F[s_fbase[t] + (long long)z * s_plane[t] + (long long)y * s_nx[t] + x];
+            if (sp.inside(t, x, y, z)) f[m] = P.F[P.desc[sp.inst[t]].in_off + sp.at(t, x, y, z)];
         }
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const int r = tid + m * kInitThreads, t = r / G::V;
+            const int r = tid + m * kSpanThreads, t = r / G::V;
             const long long e = g0 * G::V + r;
             const bool pass = f[m] > T(0);
             if (e < total) {
-                P.tau_t[e] = pass ? T(s_h[t]) / f[m] : Num<T>::inf();
+                P.tau_t[e] = pass ? T(P.desc[sp.inst[t]].h) / f[m] : Num<T>::inf();
                 P.phi_t[e] = Num<T>::inf();
             }
             if (P.ordered) {   // a warp's 32 nodes lie in one tile
@@ -207,10 +217,10 @@ __global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
             }
         }
         __syncthreads();
-        if (tid < NT && g0 + tid < P.n_tiles) {
+        if (tid < kSpan && g0 + tid < P.n_tiles) {
             const long long g = g0 + tid;
-            const int b = s_inst[tid];
-            if (s_l[tid] == 0) P.scale_done[b] = 0;        // k_scale's completion count of this instance
+            const int b = sp.inst[tid];
+            if (sp.l[tid] == 0) P.scale_done[b] = 0;       // k_scale's completion count of this instance
             P.tile_inst[g] = b;
             P.tstate[g] = kDistant;
             P.tstamp[g] = 0;
@@ -219,11 +229,11 @@ __global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
             if (P.ordered)
                 reinterpret_cast<float4 *>(P.tile_fstat)[g] = make_float4(s_acc[tid][0], s_acc[tid][1], s_acc[tid][2], s_acc[tid][3]);
         }
-        if (tid < 8 * NT && g0 + tid / 8 < P.n_tiles) {   // tile records: neighbours, instance, key scale
+        if (tid < 8 * kSpan && g0 + tid / 8 < P.n_tiles) {   // tile records: neighbours, instance, key scale
             const int t = tid / 8, k = tid % 8;
             const int g = (int)(g0 + t);
-            const InstDesc &d = P.desc[s_inst[t]];
-            const int tx = s_tc[t][0], ty = s_tc[t][1], tz = s_tc[t][2];
+            const InstDesc &d = P.desc[sp.inst[t]];
+            const int tx = sp.tc[t][0], ty = sp.tc[t][1], tz = sp.tc[t][2];
             int nb;
             switch (k) {
                 case 0: nb = tx > 0 ? g - 1 : -1; break;
@@ -232,7 +242,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
                 case 3: nb = ty + 1 < d.ty ? g + d.tx : -1; break;
                 case 4: nb = tz > 0 ? g - d.tx * d.ty : -1; break;
                 case 5: nb = tz + 1 < d.tz ? g + d.tx * d.ty : -1; break;
-                case 6: nb = s_inst[t]; break;
+                case 6: nb = sp.inst[t]; break;
                 default: nb = __float_as_int(1.0f); break;   // key scale, set by k_tile_scale
             }
             P.tile_nb[8 * (long long)g + k] = nb;
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init(FwdParams<T> P) {
             const int k0 = (int)(offsetof(Ctl, kmin) / sizeof(int)), k1 = (int)(offsetof(Ctl, rkmin) / sizeof(int)) + 3;
             reinterpret_cast<unsigned *>(P.ctl)[tid] = (tid >= k0 && tid < k1) ? kKeyInf : 0u;
         }
-        __syncthreads();                                       // the tile table is rewritten next
+        __syncthreads();                                       // the span is refilled next
     }
 }
 
@@ -584,60 +594,32 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     flush_stats<T>(P, 0, 0, t, s, d);
 }
 
-// Output: bricked phi -> the caller's row-major phi.  A CTA takes
-// kUnpackTiles consecutive bricks at a time (one contiguous block): one thread
-// per brick works out where the brick lies in its instance's grid, then every
-// thread moves kUnpackTiles * V / kUnpackThreads nodes, all loads (coalesced,
-// streaming) issued before the stores (32-byte rows of a tile for BX = 8 FP32).
-constexpr int kUnpackThreads = 256;
-constexpr int kUnpackTiles = 4;
-
+// Output: bricked phi -> the caller's row-major phi.  A CTA takes kSpan
+// consecutive bricks at a time (one contiguous block); every thread loads its
+// kSpan * V / kSpanThreads nodes at once (coalesced, streaming), then stores
+// them (rows of BX nodes of the caller's grid).
 template <class T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(kUnpackThreads) k_unpack(FwdParams<T> P) {
+__global__ void __launch_bounds__(kSpanThreads) k_unpack(FwdParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
-    constexpr int PER = kUnpackTiles * G::V / kUnpackThreads;
-    static_assert(kUnpackTiles * G::V % kUnpackThreads == 0, "whole nodes per thread");
-    __shared__ long long s_base[kUnpackTiles];     // output offset of the brick's node (0, 0, 0)
-    __shared__ int s_lim[kUnpackTiles][3];         // nodes of the brick inside the grid per axis
-    __shared__ int s_nx[kUnpackTiles];
-    __shared__ long long s_plane[kUnpackTiles];
-    for (long long g0 = (long long)blockIdx.x * kUnpackTiles; g0 < P.n_tiles; g0 += (long long)gridDim.x * kUnpackTiles) {
-        if (threadIdx.x < kUnpackTiles) {
-            const long long g = g0 + threadIdx.x;
-            int lx = 0, ly = 0, lz = 0, nx = 0;
-            long long base = 0, plane = 0;
-            if (g < P.n_tiles) {
-                const InstDesc &d = P.desc[P.tile_inst[g]];
-                const long long l = g - d.tile_base;
-                const int tx = (int)(l % d.tx), ty = (int)((l / d.tx) % d.ty), tz = (int)(l / ((long long)d.tx * d.ty));
-                lx = min(BX, d.nx - tx * BX); ly = min(BY, d.ny - ty * BY); lz = min(BZ, d.nz - tz * BZ);
-                nx = d.nx;
-                plane = (long long)d.nx * d.ny;
-                base = d.out_off + (long long)tz * BZ * plane + (long long)ty * BY * d.nx + (long long)tx * BX;
-            }
-            s_base[threadIdx.x] = base;
-            s_lim[threadIdx.x][0] = lx; s_lim[threadIdx.x][1] = ly; s_lim[threadIdx.x][2] = lz;
-            s_nx[threadIdx.x] = nx;
-            s_plane[threadIdx.x] = plane;
-        }
+    constexpr int PER = kSpan * G::V / kSpanThreads;
+    __shared__ TileSpan<BX, BY, BZ> sp;
+    const long long total = (long long)P.n_tiles * G::V;
+    for (long long g0 = (long long)blockIdx.x * kSpan; g0 < P.n_tiles; g0 += (long long)gridDim.x * kSpan) {
+        if (threadIdx.x < kSpan) sp.fill(P.desc, P.B, P.n_tiles, g0, threadIdx.x);
         __syncthreads();
-        const long long e0 = g0 * G::V;
-        const long long total = (long long)P.n_tiles * G::V;
         T val[PER];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const long long e = e0 + threadIdx.x + (long long)m * kUnpackThreads;
+            const long long e = g0 * G::V + threadIdx.x + (long long)m * kSpanThreads;
             val[m] = e < total ? __ldcs(P.phi_t + e) : T(0);
         }
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-            const int r = threadIdx.x + m * kUnpackThreads;        // node within this CTA's block
-            const int t = r / G::V, q = r % G::V;
+            const int r = threadIdx.x + m * kSpanThreads, t = r / G::V, q = r % G::V;
             const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
-            if (x < s_lim[t][0] && y < s_lim[t][1] && z < s_lim[t][2])
-                P.phi_out[s_base[t] + (long long)z * s_plane[t] + (long long)y * s_nx[t] + x] = val[m];
+            if (sp.inside(t, x, y, z)) P.phi_out[P.desc[sp.inst[t]].out_off + sp.at(t, x, y, z)] = val[m];
         }
-        __syncthreads();                                            // the brick table is rewritten next
+        __syncthreads();                                            // the span is refilled next
     }
 }
 

@@ -146,3 +146,19 @@ def test_backtrace_argument_errors_before_device_work():
     bad = _lib.grids_array([(8, 8, 8, (0.1, -1.0, 0.1))])
     assert lib.eik_backtrace(bad, 0, 1, 1, 1, 4, 1, 1, None) == E                      # spacing
     assert lib.eik_backtrace(g, 0, 1, None, 0, 4, None, None, None) == _lib.EIK_OK     # nothing to do
+
+
+def test_adjoint_gradient_blocks_equal_or_disjoint():
+    """eik_adjoint_batched rejects gradient blocks that partly overlap, or that
+    share an offset with different dims, before any device work."""
+    lib = _lib.load()
+    o = _lib.make_options()
+    so = _lib.i64_array([0, 0, 0])
+    zero = _lib.i64_array([0, 0])
+    for dims, goff in (([(8, 8, 8, 0.1), (8, 8, 8, 0.1)], [0, 100]),
+                       ([(8, 8, 8, 0.1), (8, 8, 4, 0.1)], [0, 0]),
+                       ([(8, 8, 8, 0.1), (8, 8, 8, 0.1)], [600, 100])):
+        g = _lib.grids_array(dims)
+        rc = lib.eik_adjoint_batched(2, g, 4096, zero, 4096, zero, None, so, 4096, 4096, _lib.i64_array(goff),
+                                     4096, 1 << 40, None, ctypes.byref(o), None)
+        assert rc == _lib.EIK_ERR_ARG and b"gradient blocks" in lib.eik_last_error(), (dims, goff)
