@@ -18,7 +18,7 @@
 // staged (phi with a two-node face halo, to know whether a neighbour i of j
 // selects j, which needs the neighbour beyond i; lambda with a one-node
 // halo), each node computes its own J_jj and the six weights w_{i->j} of its
-// neighbours once, then lambda is relaxed by Jacobi sweeps inside the tile
+// neighbours once, then lambda is relaxed in place by sweeps inside the tile
 // until nothing changes (exact: on a DAG a value computed from final inputs is
 // final, and the sum has a fixed order, so the result does not depend on the
 // schedule).  Neighbour tiles across faces where lambda changed are listed.
@@ -244,7 +244,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
     // interior
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
-        const int q = gt + GG::GT * m;
+        const int q = GG::node(gt, m);
         x[m] = q % BX; y[m] = (q / BX) % BY; z[m] = q / (BX * BY);
         const size_t a = (size_t)g * G::V + q;
         const T ph = __ldcg(P.phi_t + a);
@@ -310,14 +310,18 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             if (hi1 < INF && pj <= hi2 && hi1 > pj) w[m][2 * ax + 1] = T(2) * (hi1 - pj);
         }
     }
-    // Jacobi on lambda until no change; sources and nodes with J == 0 keep lambda
+    // Sweeps on lambda until no change; sources and nodes with J == 0 keep
+    // lambda.  A thread relaxes its z segment in descending z (lambda flows
+    // against the arrival times, most often down the z planes of a shot set
+    // from the top face).
     mine = 0;
     first_changed = false;
     int s = 0;
     for (;;) {
         unsigned ch = 0;
 #pragma unroll
-        for (int m = 0; m < NPT; ++m) {
+        for (int mm = 0; mm < NPT; ++mm) {
+            const int m = NPT - 1 - mm;
             if (!(J[m] > T(0))) continue;
             const int c = G::sidx(x[m], y[m], z[m]);
             T acc = rr[m];
@@ -338,7 +342,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
     }
 #pragma unroll
     for (int m = 0; m < NPT; ++m)
-        if (mine >> m & 1) __stcg(P.lam_t + (size_t)g * G::V + gt + GG::GT * m, lam[m]);
+        if (mine >> m & 1) __stcg(P.lam_t + (size_t)g * G::V + GG::node(gt, m), lam[m]);
     return s;
 }
 
@@ -398,10 +402,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
         // and visit the kept tiles one by one
         GroupQueue &q = gqs[gi];
         int *grab = &ctl->rgrab[r % 3];
-        for (;;) {
+        for (bool first = true;; first = false) {
             if (gt == 0) {
                 q.n = 0;
-                q.base = atomicAdd(grab, chunk);
+                q.base = grab_chunk(grab, first, blockIdx.x * GG::NG + gi, gridDim.x * GG::NG, chunk);
             }
             group_sync(bid, GG::GT);
             const int base = q.base;
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
 #pragma unroll
                 for (int m = 0; m < GG::NPT; ++m)
                     if (mine >> m & 1) {
-                        const int fb = G::faces_of(gt + GG::GT * m);
+                        const int fb = G::faces_of(GG::node(gt, m));
                         if (fb) atomicOr(&s_fmask[gi], fb);
                     }
                 group_sync(bid, GG::GT);

@@ -31,6 +31,18 @@ struct GroupGeom {
     static constexpr int NG = CTA / GT;                    // groups per CTA
     static constexpr int NPT = G::V / GT;                  // nodes per thread
     static_assert(NG <= kWarpsPerCta && NG <= 8, "one staged block per group");
+    // Node of slot m of group thread gt.  Where the tile's (x, y) columns
+    // divide the group, a thread owns NPT consecutive z planes of one column,
+    // and a sweep relaxes them in ascending z: within the thread a sweep is
+    // Gauss-Seidel along z, so a front moving up the tile crosses NPT planes
+    // per sweep instead of one (measured: 10 % fewer sweeps on the 3D
+    // workloads, 5 % less time).  Otherwise slot m is node gt + GT m.
+    static constexpr int PLANE = BX * BY;
+    static constexpr bool ZSEG = GT % PLANE == 0 && (GT / PLANE) * NPT == BZ;
+    static __device__ __forceinline__ int node(int gt, int m) {
+        if constexpr (ZSEG) return gt % PLANE + PLANE * ((gt / PLANE) * NPT + m);
+        else return gt + GT * m;
+    }
 };
 
 struct GroupCtl {
@@ -69,7 +81,7 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     const T *tg = P.tau_t + (size_t)g * G::V;
 #pragma unroll
     for (int m = 0; m < GG::NPT; ++m) {
-        const int q = gt + GG::GT * m;
+        const int q = GG::node(gt, m);
         v[m] = __ldcg(pg + q);
         tau[m] = __ldcg(tg + q);
         c[m] = G::sidx_of(q);
@@ -105,7 +117,7 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     }
 #pragma unroll
     for (int m = 0; m < GG::NPT; ++m)
-        if (mine >> m & 1) __stcg(P.phi_t + (size_t)g * G::V + gt + GG::GT * m, v[m]);
+        if (mine >> m & 1) __stcg(P.phi_t + (size_t)g * G::V + GG::node(gt, m), v[m]);
     return s;
 }
 
@@ -134,6 +146,15 @@ struct GroupQueue {
     int n;
     int base;
 };
+
+// Start of a group's next chunk of the list.  The first chunk of every group
+// is static (its index among the launch's groups), the others come from a
+// shared counter that starts after all the first chunks: the first grab of an
+// iteration costs no atomic round trip, and a group whose first chunk lies
+// past the end of the list learns so without one.
+__device__ __forceinline__ int grab_chunk(int *grab, bool first, int group, int groups, int chunk) {
+    return first ? group * chunk : groups * chunk + atomicAdd(grab, chunk);
+}
 
 // List entries per grab: about one visit per chunk at the previous
 // iteration's visit rate (deferred entries are cheap, visits are not), at most
@@ -173,10 +194,11 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
     const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
     chunk = max(1, min(chunk, GG::GT));
-    for (;;) {
+    const int cta_groups = blockDim.x / GG::GT;
+    for (bool first = true;; first = false) {
         if (gt == 0) {
             q.n = 0;
-            q.base = atomicAdd(grab, chunk);
+            q.base = grab_chunk(grab, first, blockIdx.x * cta_groups + gi, gridDim.x * cta_groups, chunk);
         }
         group_sync(bid, GG::GT);
         const int base = q.base;
@@ -230,7 +252,7 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
                     if (ord.on) {
 #pragma unroll
                         for (int m = 0; m < GG::NPT; ++m) {
-                            const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                            const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
                             for (int f = 0; f < 6; ++f)
                                 if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
                         }
@@ -254,7 +276,7 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
 #pragma unroll
                 for (int m = 0; m < GG::NPT; ++m) {
                     if (!(mine >> m & 1)) continue;
-                    const int fb = node_faces_q<BX, BY, BZ>(gt + GG::GT * m);
+                    const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
                     if (fb) {
                         atomicOr(&gc.fmask, fb);
                         if (ord.on)
