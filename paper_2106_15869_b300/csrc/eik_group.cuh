@@ -36,7 +36,8 @@ struct GroupGeom {
     // and a sweep relaxes them in ascending z: within the thread a sweep is
     // Gauss-Seidel along z, so a front moving up the tile crosses NPT planes
     // per sweep instead of one (measured: 10 % fewer sweeps on the 3D
-    // workloads, 5 % less time).  Otherwise slot m is node gt + GT m.
+    // workloads, 5 % less time; group_visit picks descending z for fronts
+    // coming from above).  Otherwise slot m is node gt + GT m.
     static constexpr int PLANE = BX * BY;
     static constexpr bool ZSEG = GT % PLANE == 0 && (GT / PLANE) * NPT == BZ;
     static __device__ __forceinline__ int node(int gt, int m) {
@@ -94,13 +95,21 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
         sm[slot] = (unsigned)n < (unsigned)P.n_tiles ? __ldcg(P.phi_t + (size_t)n * G::V + src) : Num<T>::inf();
     }
     group_sync(bid, GG::GT);
+    // z order of the segments: descending when the front comes from above
+    // (the halo above the thread's column is lower than the one below, by a
+    // majority of the warp, so that the warp does not diverge)
+    bool down = false;
+    if constexpr (GG::ZSEG && GG::NPT > 1) {
+        const int col = G::sidx_of(gt % GG::PLANE);          // the column's node z = 0
+        const T below = sm[col - G::SX * G::SY], above = sm[col + BZ * G::SX * G::SY];
+        down = __popc(__ballot_sync(kFull, above < below)) > 16;
+    }
     mine = 0;
     first_changed = false;
     int s = 0;
     for (;;) {
         unsigned ch = 0;
-#pragma unroll
-        for (int m = 0; m < GG::NPT; ++m) {
+        auto relax = [&](int m) {
             if (!(tau[m] < T(0))) {
                 const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
                 const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
@@ -108,6 +117,13 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
                 const T u = node_solve(ax, ay, az, tau[m], P.mt);
                 if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
             }
+        };
+        if (down) {
+#pragma unroll
+            for (int m = GG::NPT - 1; m >= 0; --m) relax(m);
+        } else {
+#pragma unroll
+            for (int m = 0; m < GG::NPT; ++m) relax(m);
         }
         mine |= ch;
         ++s;
