@@ -329,8 +329,11 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             acc += w[m][1] * sm.lam[c + 1];
             acc += w[m][2] * sm.lam[c - G::SX];
             acc += w[m][3] * sm.lam[c + G::SX];
-            acc += w[m][4] * sm.lam[c - G::SX * G::SY];
-            acc += w[m][5] * sm.lam[c + G::SX * G::SY];
+            // z neighbours inside the thread's own segment come from registers
+            const T lzlo = (GG::ZSEG && m > 0) ? lam[m > 0 ? m - 1 : 0] : sm.lam[c - G::SX * G::SY];
+            const T lzhi = (GG::ZSEG && m + 1 < NPT) ? lam[m + 1 < NPT ? m + 1 : m] : sm.lam[c + G::SX * G::SY];
+            acc += w[m][4] * lzlo;
+            acc += w[m][5] * lzhi;
             const T nl = acc / J[m];
             if (nl != lam[m]) { lam[m] = nl; sm.lam[c] = nl; ch |= 1u << m; }
         };
