@@ -105,7 +105,7 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
 // workspace regions (byte offsets), all 256-byte aligned
 struct Layout {
     size_t ctl, desc, tile_fstat, inst_scale, scale_part, scale_done, tile_inst, tile_nb, tstate, tstamp, tkey, list0,
-        list1, phi_t, tau_t;
+        list1, vlist, phi_t, tau_t;
     size_t q_data, q_seq, q_state, total;
     long long n_tiles;
     unsigned long long q_slots;
@@ -185,6 +185,7 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     L.tkey = take(2 * 4 * (size_t)tiles);
     L.list0 = take(4 * (size_t)tiles);
     L.list1 = take(4 * (size_t)tiles);
+    L.vlist = take(4 * (size_t)tiles);
     L.phi_t = take(esz * (size_t)(tiles * V));
     L.tau_t = take(esz * (size_t)(tiles * V));
     // work queue of the asynchronous schedule: 2^k slots > tiles + any number of warps
@@ -301,6 +302,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.order = o.order;
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
     P.list1 = reinterpret_cast<int *>(ws + L.list1);
+    P.vlist = reinterpret_cast<int *>(ws + L.vlist);
     P.phi_t = reinterpret_cast<T *>(ws + L.phi_t);
     P.tau_t = reinterpret_cast<T *>(ws + L.tau_t);
     P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);

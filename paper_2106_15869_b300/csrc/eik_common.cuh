@@ -74,6 +74,8 @@ struct Ctl {
     int q_pending;                       // tiles queued or being visited in the current phase
     int q_stop;                          // the visit cap was reached: every warp leaves the phase
     long long q_visits;                  // visits in the current phase (cap check)
+    int vcnt[3], vgrab[3];               // two-phase Step-2 iterations: kept tiles listed / taken, slot it % 3
+    int rvcnt[3], rvgrab[3];             // the same for Step 3
 };
 static_assert(sizeof(Ctl) <= 256, "the control block is zeroed by 64 threads");
 

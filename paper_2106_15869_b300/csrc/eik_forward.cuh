@@ -50,6 +50,7 @@ struct FwdParams {
     int ordered;                 // 1 = bucketed order of the lists
     float order;                 // bucket width in tile-crossing times
     int *list0, *list1;
+    int *vlist;                  // the tiles kept by the classification of a two-phase iteration
     T *phi_t, *tau_t;
     Ctl *ctl;
     long long max_iters;

@@ -191,6 +191,88 @@ __device__ __forceinline__ int group_chunk(int n, int visited_prev, int listed_p
     return max(1, min(c, gt));
 }
 
+// Visit the tile the group fetched into gc and update the lists: Step 2 (the
+// tile stays Active after a visit that changed it, else joins Source and
+// activates its Distant face neighbours) or Step 3 (`remedy`: the face
+// neighbours whose halo dropped are listed, the tile itself if the sweep cap
+// stopped it).
+template <class T, int BX, int BY, int BZ, bool remedy, int GTM>
+__device__ __forceinline__ void visit_and_list(const FwdParams<T> &P, T *sm, GroupCtl &gc, int gt, int bid,
+                                               const OrderCtx &ord, unsigned *knext, int *out, int *cnt_next,
+                                               unsigned *kmin_next, int next_stamp, int *s_visits,
+                                               long long &st_tiles, long long &st_sweeps) {
+    using GG = GroupGeom<BX, BY, BZ, GTM>;
+    Ctl *ctl = P.ctl;
+    const int g = gc.tile;
+    const unsigned key = gc.key;
+    T v[GG::NPT];
+    unsigned mine;
+    bool changed;
+    const int s = group_visit<T, BX, BY, BZ, GTM>(P, sm, gc, g, gt, bid, v, mine, changed);
+    if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
+    if (!remedy) {
+        if (changed && (!P.one_visit || s >= P.max_sweeps)) {
+            // stays Active; its next visit confirms (or not) that it converged
+            if (gt < 32) {
+                if (ord.on && gt == 0) atomicMin(knext + g, key);
+                warp_push(ctl, cnt_next, out, P.n_tiles, gt == 0, g, ord.on ? kmin_next : nullptr, key);
+            }
+        } else {
+            // converged: Active -> Source, Distant face neighbours become Active
+            if (ord.on) {
+#pragma unroll
+                for (int m = 0; m < GG::NPT; ++m) {
+                    const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
+                    for (int f = 0; f < 6; ++f)
+                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+                }
+                group_sync(bid, GG::GT);
+            }
+            if (gt < 32) {
+                if (gt == 0) __stcg(P.tstate + g, (int)kSource);
+                const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
+                const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
+                const bool act = prev == (int)kDistant;
+                unsigned kf = kKeyInf;
+                if (ord.on && nbf >= 0) {
+                    kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                    if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
+                }
+                warp_push(ctl, cnt_next, out, P.n_tiles, act, nbf, ord.on ? kmin_next : nullptr, kf);
+            }
+        }
+    } else {
+        // faces where a node dropped, and (ordered) the smallest dropped value on each
+#pragma unroll
+        for (int m = 0; m < GG::NPT; ++m) {
+            if (!(mine >> m & 1)) continue;
+            const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
+            if (fb) {
+                atomicOr(&gc.fmask, fb);
+                if (ord.on)
+                    for (int f = 0; f < 6; ++f)
+                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
+            }
+        }
+        group_sync(bid, GG::GT);
+        if (gt < 32) {
+            const int fm = gc.fmask;
+            int cand = -1;
+            if (gt < 6 && (fm >> gt & 1) && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles) cand = gc.nb[gt];
+            if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+            unsigned kc = kKeyInf;
+            if (ord.on && cand >= 0) {
+                kc = gt == 6 ? key : scaled_key(key_dec(gc.fmin[gt]), gc.scale);
+                atomicMin(knext + cand, kc);
+            }
+            const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+            if (ord.on && cand >= 0 && !want) atomicMin(kmin_next, kc);
+            warp_push(ctl, cnt_next, out, P.n_tiles, want, cand, ord.on ? kmin_next : nullptr, kc);
+        }
+    }
+    group_sync(bid, GG::GT);                           // the visit is done with gc
+}
+
 // Latency-mode iteration over a list: every thread group takes chunks of the
 // list from a shared counter (dynamic balance: visits differ in length by an
 // order of magnitude), classifies a chunk with all its threads at once (a
@@ -259,76 +341,90 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
         for (int qi = 0; qi < qn; ++qi) {
             if (gt == 0) group_fetch(P, gc, q.tile[qi], q.key[qi]);
             group_sync(bid, GG::GT);
-            const int g = gc.tile;
-            const unsigned key = gc.key;
-            T v[GG::NPT];
-            unsigned mine;
-            bool changed;
-            const int s = group_visit<T, BX, BY, BZ, GTM>(P, sm, gc, g, gt, bid, v, mine, changed);
-            if (gt == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
-            if (!remedy) {
-                if (changed && (!P.one_visit || s >= P.max_sweeps)) {
-                    // stays Active; its next visit confirms (or not) that it converged
-                    if (gt < 32) {
-                        if (ord.on && gt == 0) atomicMin(knext + g, key);
-                        warp_push(ctl, cnt_next, out, P.n_tiles, gt == 0, g, ord.on ? kmin_next : nullptr, key);
-                    }
-                } else {
-                    // converged: Active -> Source, Distant face neighbours become Active
-                    if (ord.on) {
-#pragma unroll
-                        for (int m = 0; m < GG::NPT; ++m) {
-                            const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
-                            for (int f = 0; f < 6; ++f)
-                                if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-                        }
-                        group_sync(bid, GG::GT);
-                    }
-                    if (gt < 32) {
-                        if (gt == 0) __stcg(P.tstate + g, (int)kSource);
-                        const int nbf = gt < 6 && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles ? gc.nb[gt] : -1;
-                        const int prev = nbf >= 0 ? atomicCAS(P.tstate + nbf, (int)kDistant, (int)kActive) : (int)kSource;
-                        const bool act = prev == (int)kDistant;
-                        unsigned kf = kKeyInf;
-                        if (ord.on && nbf >= 0) {
-                            kf = scaled_key(key_dec(gc.fmin[gt]), gc.scale);
-                            if (act || prev == (int)kActive) atomicMin(knext + nbf, kf);
-                        }
-                        warp_push(ctl, cnt_next, out, P.n_tiles, act, nbf, ord.on ? kmin_next : nullptr, kf);
-                    }
-                }
-            } else {
-                // faces where a node dropped, and (ordered) the smallest dropped value on each
-#pragma unroll
-                for (int m = 0; m < GG::NPT; ++m) {
-                    if (!(mine >> m & 1)) continue;
-                    const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
-                    if (fb) {
-                        atomicOr(&gc.fmask, fb);
-                        if (ord.on)
-                            for (int f = 0; f < 6; ++f)
-                                if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-                    }
-                }
-                group_sync(bid, GG::GT);
-                if (gt < 32) {
-                    const int fm = gc.fmask;
-                    int cand = -1;
-                    if (gt < 6 && (fm >> gt & 1) && (unsigned)gc.nb[gt] < (unsigned)P.n_tiles) cand = gc.nb[gt];
-                    if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
-                    unsigned kc = kKeyInf;
-                    if (ord.on && cand >= 0) {
-                        kc = gt == 6 ? key : scaled_key(key_dec(gc.fmin[gt]), gc.scale);
-                        atomicMin(knext + cand, kc);
-                    }
-                    const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
-                    if (ord.on && cand >= 0 && !want) atomicMin(kmin_next, kc);
-                    warp_push(ctl, cnt_next, out, P.n_tiles, want, cand, ord.on ? kmin_next : nullptr, kc);
-                }
-            }
-            group_sync(bid, GG::GT);                   // the visit is done with gc (and q, after the last)
+            visit_and_list<T, BX, BY, BZ, remedy, GTM>(P, sm, gc, gt, bid, ord, knext, out, cnt_next, kmin_next,
+                                                       next_stamp, s_visits, st_tiles, st_sweeps);
         }
     }
+}
+
+// An iteration of the latency-only kernel with more visits expected than
+// thread groups, in two phases split by a grid barrier.  First every thread
+// of the launch classifies list entries (a deferred entry is listed again on
+// the spot, a kept one is appended to the visit list); then the thread groups
+// take the kept tiles one at a time (the first by group index, the others from
+// a shared counter).  Taking chunks of the list with the visits they hold
+// (group_pass) leaves some groups with several long visits while others idle:
+// measured on the 256^3 oscillating workload, the slowest group of a Step-3
+// iteration made 3.8 visits against 2.3 on average and the iteration lasted
+// twice the median group's time.  Returns false if the grid barrier timed out.
+template <class T, int BX, int BY, int BZ, bool remedy, int GTM>
+__device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, int it, int n, unsigned kmin_cur,
+                                 float width, int *s_visits, long long &st_tiles, long long &st_sweeps,
+                                 long long &st_def, unsigned long long &target) {
+    using G = TileGeom<BX, BY, BZ>;
+    using GG = GroupGeom<BX, BY, BZ, GTM>;
+    Ctl *ctl = P.ctl;
+    const int slot = it % 3, nslot = (it + 1) % 3;
+    const int *in = (it & 1) ? P.list1 : P.list0;
+    int *out = (it & 1) ? P.list0 : P.list1;
+    unsigned *kcur = P.tkey + (size_t)(it & 1) * P.n_tiles;
+    unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
+    int *cnt_next = remedy ? &ctl->rcnt[nslot] : &ctl->cnt[nslot];
+    unsigned *kmin_next = remedy ? &ctl->rkmin[nslot] : &ctl->kmin[nslot];
+    int *vcnt = remedy ? &ctl->rvcnt[slot] : &ctl->vcnt[slot];
+    int *vgrab = remedy ? &ctl->rvgrab[slot] : &ctl->vgrab[slot];
+    const int next_stamp = it + 2;
+    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    n = min(n, P.n_tiles);
+    // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the pushes)
+    const int lane = threadIdx.x & 31;
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
+        const int e = e0 + lane;
+        const bool valid = e < n;
+        const int g = valid ? __ldcg(in + e) : -1;
+        const unsigned key = valid && ord.on ? __ldcg(kcur + g) : kKeyInf;
+        const bool defer = valid && ord.on && !order_visit(ord, key);
+        bool want = false;
+        if (defer) {
+            __stcg(kcur + g, kKeyInf);                 // no one writes this parity in this iteration
+            atomicMin(knext + g, key);
+            want = remedy ? atomicExch(P.tstamp + g, next_stamp) != next_stamp : true;
+            st_def++;
+        }
+        warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
+        warp_push(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g);   // its key stays in kcur
+    }
+    if (!grid_sync(ctl, target)) return false;
+    // visit the kept tiles
+    const int tid = threadIdx.x;
+    const int gi = tid / GG::GT, gt = tid % GG::GT, bid = 1 + gi;
+    T *sm = smbase + (size_t)gi * G::S;
+    GroupCtl &gc = gcs[gi];
+    const int cta_groups = blockDim.x / GG::GT;
+    const int groups = gridDim.x * cta_groups;
+    const int nv = min(ld_volatile(vcnt), P.n_tiles);
+    for (bool first = true;; first = false) {
+        if (gt == 0) {
+            const int idx = first ? blockIdx.x * cta_groups + gi : groups + atomicAdd(vgrab, 1);
+            if (idx < nv) {
+                const int g = __ldcg(P.vlist + idx);
+                unsigned key = kKeyInf;
+                if (ord.on) {
+                    key = __ldcg(kcur + g);
+                    __stcg(kcur + g, kKeyInf);
+                }
+                group_fetch(P, gc, g, key);
+            } else {
+                gc.tile = -1;
+            }
+        }
+        group_sync(bid, GG::GT);
+        if (gc.tile < 0) break;                        // group-uniform
+        visit_and_list<T, BX, BY, BZ, remedy, GTM>(P, sm, gc, gt, bid, ord, knext, out, cnt_next, kmin_next,
+                                                   next_stamp, s_visits, st_tiles, st_sweeps);
+    }
+    return true;
 }
 
 template <class T, int BX, int BY, int BZ, int GTM = kGroupThreads>

@@ -392,7 +392,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
     init_stage<T, BX, BY, BZ>(my);
     if (threadIdx.x == 0) s_visits = 0;
     const int groups = gridDim.x * GroupGeom<BX, BY, BZ>::NG;
-    const int groups_s = gridDim.x * GGS::NG;
     float width = 1.0f;
     int n_prev = 0;
     long long tk = 0;
@@ -413,7 +412,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
         const unsigned kq = s_k;
         if (it > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
         const int chunk = group_chunk(n, it > 0 ? s_p : 0, it > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
-        const int listed_prev = n_prev;
         n_prev = n;
         if (n == 0) break;
         if (it >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
@@ -421,16 +419,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
             ctl->cnt[(it + 2) % 3] = 0;
             ctl->kmin[(it + 2) % 3] = kKeyInf;
             ctl->grab[(it + 2) % 3] = 0;
+            ctl->vcnt[(it + 2) % 3] = 0;
+            ctl->vgrab[(it + 2) % 3] = 0;
             ctl->nproc[(it + 2) % 4] = 0;
         }
         if constexpr (MODE == kPersistLatency) {
-            // more visits expected (the last iteration's, or the list) than groups: smaller groups
-            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (it > 0 ? s_p : n) > groups)
-                update_pass_group<T, BX, BY, BZ, kSmallGroupThreads>(
-                    P, &sm.phi[0][0], gcs, gqs, it, n, kq, width,
-                    group_chunk(n, it > 0 ? s_p : 0, it > 0 ? listed_prev : 0, groups_s, GGS::GT), &s_visits, t_upd,
-                    sweeps, deferred);
-            else
+            // more visits expected (the last iteration's, or the list) than groups: smaller
+            // groups, and the two-phase pass (classify the whole list, then one visit per grab)
+            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (it > 0 ? s_p : n) > groups) {
+                if (!group_pass_split<T, BX, BY, BZ, false, kSmallGroupThreads>(
+                        P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred, target))
+                    goto done;
+            } else
                 update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits,
                                                  t_upd, sweeps, deferred);
         } else if (n <= kGroupModeFactor * groups) {
@@ -468,7 +468,6 @@ neighbour_check:
         const unsigned kq = s_k;
         if (r > 0) width = adapt_window(width, s_p, n_prev, groups, (int)gridDim.x * kWarpsPerCta);
         const int chunk = group_chunk(n, r > 0 ? s_p : 0, r > 0 ? n_prev : 0, groups, GroupGeom<BX, BY, BZ>::GT);
-        const int listed_prev = n_prev;
         n_prev = n;
         if (n == 0) break;
         if (r >= P.max_iters) { if (threadIdx.x == 0) atomicOr(&ctl->flags, kFlagCap); goto done; }
@@ -476,15 +475,16 @@ neighbour_check:
             ctl->rcnt[(r + 2) % 3] = 0;
             ctl->rkmin[(r + 2) % 3] = kKeyInf;
             ctl->rgrab[(r + 2) % 3] = 0;
+            ctl->rvcnt[(r + 2) % 3] = 0;
+            ctl->rvgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
         if constexpr (MODE == kPersistLatency) {
-            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (r > 0 ? s_p : n) > groups)
-                remedy_pass_group<T, BX, BY, BZ, kSmallGroupThreads>(
-                    P, &sm.phi[0][0], gcs, gqs, r, n, kq, width,
-                    group_chunk(n, r > 0 ? s_p : 0, r > 0 ? listed_prev : 0, groups_s, GGS::GT), &s_visits, t_rem,
-                    sweeps, deferred);
-            else
+            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (r > 0 ? s_p : n) > groups) {
+                if (!group_pass_split<T, BX, BY, BZ, true, kSmallGroupThreads>(
+                        P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t_rem, sweeps, deferred, target))
+                    goto done;
+            } else
                 remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits,
                                                  t_rem, sweeps, deferred);
         } else if (n <= kGroupModeFactor * groups) {
