@@ -407,7 +407,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
         // and visit the kept tiles one by one
         GroupQueue &q = gqs[gi];
         int *grab = &ctl->rgrab[r % 3];
+        // the static first chunks cover the list: no grab from the shared counter
+        const bool static_only = (long long)gridDim.x * GG::NG * chunk >= n;
         for (bool first = true;; first = false) {
+            if (!first && static_only) break;
             if (gt == 0) {
                 q.n = 0;
                 q.base = grab_chunk(grab, first, blockIdx.x * GG::NG + gi, gridDim.x * GG::NG, chunk);

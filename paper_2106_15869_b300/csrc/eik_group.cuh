@@ -148,17 +148,19 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
 }
 
 // Thread 0 of the group: the record (neighbours, key scale) of tile g.
-template <class T>
-__device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc, int g, unsigned key) {
+__device__ __forceinline__ void group_set(GroupCtl &gc, int g, unsigned key, int4 r0, int4 r1) {
     gc.tile = g;
     gc.key = key;
-    const int4 r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g));
-    const int4 r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4));
     gc.nb[0] = r0.x; gc.nb[1] = r0.y; gc.nb[2] = r0.z; gc.nb[3] = r0.w; gc.nb[4] = r1.x; gc.nb[5] = r1.y;
     gc.scale = __int_as_float(r1.w);
     gc.fmask = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) gc.fmin[f] = kKeyInf;
+}
+template <class T>
+__device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc, int g, unsigned key) {
+    group_set(gc, g, key, __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g)),
+              __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4)));
 }
 
 // per-node face bits of node q
@@ -166,9 +168,11 @@ template <int BX, int BY, int BZ>
 __device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>::faces_of(q); }
 
 // Per-group queue of the tiles a group visits from the chunk of the list it took.
+constexpr int kQueueRec = 4;                           // queued tiles whose records the classification loads
 struct GroupQueue {
     int tile[kGroupThreads];
     unsigned key[kGroupThreads];
+    int4 rec[kQueueRec][2];
     int n;
     int base;
 };
@@ -303,7 +307,10 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
     n = min(n, P.n_tiles);
     chunk = max(1, min(chunk, GG::GT));
     const int cta_groups = blockDim.x / GG::GT;
+    // the static first chunks cover the list: no grab from the shared counter
+    const bool static_only = (long long)gridDim.x * cta_groups * chunk >= n;
     for (bool first = true;; first = false) {
+        if (!first && static_only) break;
         if (gt == 0) {
             q.n = 0;
             q.base = grab_chunk(grab, first, blockIdx.x * cta_groups + gi, gridDim.x * cta_groups, chunk);
@@ -311,12 +318,18 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
         group_sync(bid, GG::GT);
         const int base = q.base;
         if (base >= n) break;                          // group-uniform
-        // classify: one entry per thread (every lane of the group's warps takes part in the pushes)
+        // classify: one entry per thread (every lane of the group's warps takes part in the pushes);
+        // the tile record is loaded beside the key, for the first queued tiles
         {
             const int e = base + gt;
             const bool valid = gt < chunk && e < n;
             const int g = valid ? __ldcg(in + e) : -1;
             unsigned key = kKeyInf;
+            int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+            if (valid) {
+                r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g));
+                r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4));
+            }
             if (valid && ord.on) {
                 key = __ldcg(kcur + g);
                 __stcg(kcur + g, kKeyInf);               // no one writes this parity in this iteration
@@ -333,13 +346,17 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
                 const int pos = atomicAdd(&q.n, 1);
                 q.tile[pos] = g;
                 q.key[pos] = key;
+                if (pos < kQueueRec) { q.rec[pos][0] = r0; q.rec[pos][1] = r1; }
             }
         }
         group_sync(bid, GG::GT);
         const int qn = q.n;
         // visit
         for (int qi = 0; qi < qn; ++qi) {
-            if (gt == 0) group_fetch(P, gc, q.tile[qi], q.key[qi]);
+            if (gt == 0) {
+                if (qi < kQueueRec) group_set(gc, q.tile[qi], q.key[qi], q.rec[qi][0], q.rec[qi][1]);
+                else group_fetch(P, gc, q.tile[qi], q.key[qi]);
+            }
             group_sync(bid, GG::GT);
             visit_and_list<T, BX, BY, BZ, remedy, GTM>(P, sm, gc, gt, bid, ord, knext, out, cnt_next, kmin_next,
                                                        next_stamp, s_visits, st_tiles, st_sweeps);
