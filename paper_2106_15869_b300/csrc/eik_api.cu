@@ -185,7 +185,7 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     L.tkey = take(2 * 4 * (size_t)tiles);
     L.list0 = take(4 * (size_t)tiles);
     L.list1 = take(4 * (size_t)tiles);
-    L.vlist = take(4 * (size_t)tiles);
+    L.vlist = take(sizeof(VisitRec) * (size_t)tiles);
     L.phi_t = take(esz * (size_t)(tiles * V));
     L.tau_t = take(esz * (size_t)(tiles * V));
     // work queue of the asynchronous schedule: 2^k slots > tiles + any number of warps
@@ -302,7 +302,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.order = o.order;
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
     P.list1 = reinterpret_cast<int *>(ws + L.list1);
-    P.vlist = reinterpret_cast<int *>(ws + L.vlist);
+    P.vlist = reinterpret_cast<VisitRec *>(ws + L.vlist);
     P.phi_t = reinterpret_cast<T *>(ws + L.phi_t);
     P.tau_t = reinterpret_cast<T *>(ws + L.tau_t);
     P.ctl = reinterpret_cast<Ctl *>(ws + L.ctl);

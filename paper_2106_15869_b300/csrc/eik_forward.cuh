@@ -32,6 +32,13 @@ namespace eik {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerCta = 8;
 
+// A tile kept by the classification of a two-phase iteration: {tile, key},
+// and its record (neighbours, instance, key scale) as in tile_nb.
+struct VisitRec {
+    int4 head;
+    int4 r0, r1;
+};
+
 template <class T>
 struct FwdParams {
     const InstDesc *desc;
@@ -50,7 +57,7 @@ struct FwdParams {
     int ordered;                 // 1 = bucketed order of the lists
     float order;                 // bucket width in tile-crossing times
     int *list0, *list1;
-    int *vlist;                  // the tiles kept by the classification of a two-phase iteration
+    VisitRec *vlist;             // the tiles kept by the classification of a two-phase iteration
     T *phi_t, *tau_t;
     Ctl *ctl;
     long long max_iters;

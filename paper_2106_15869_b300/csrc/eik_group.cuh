@@ -393,24 +393,48 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     const int next_stamp = it + 2;
     const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
     n = min(n, P.n_tiles);
-    // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the pushes)
+    // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the
+    // pushes); a kept tile goes to the visit list with its key and record
     const int lane = threadIdx.x & 31;
     const int nthreads = gridDim.x * blockDim.x;
     for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
         const int e = e0 + lane;
         const bool valid = e < n;
         const int g = valid ? __ldcg(in + e) : -1;
-        const unsigned key = valid && ord.on ? __ldcg(kcur + g) : kKeyInf;
+        unsigned key = kKeyInf;
+        int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+        if (valid) {
+            r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g));
+            r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_nb + 8 * g + 4));
+        }
+        if (valid && ord.on) {
+            key = __ldcg(kcur + g);
+            __stcg(kcur + g, kKeyInf);                 // no one writes this parity in this iteration
+        }
         const bool defer = valid && ord.on && !order_visit(ord, key);
         bool want = false;
         if (defer) {
-            __stcg(kcur + g, kKeyInf);                 // no one writes this parity in this iteration
             atomicMin(knext + g, key);
             want = remedy ? atomicExch(P.tstamp + g, next_stamp) != next_stamp : true;
             st_def++;
         }
         warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
-        warp_push(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g);   // its key stays in kcur
+        const bool keep = valid && !defer;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (m) {
+            int base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(vcnt, __popc(m));
+            base = __shfl_sync(kFull, base, __ffs(m) - 1);
+            const int pos = base + __popc(m & ((1u << lane) - 1));
+            if (keep && pos < P.n_tiles) {
+                VisitRec *vr = P.vlist + pos;
+                __stcg(&vr->head, make_int4(g, (int)key, 0, 0));
+                __stcg(&vr->r0, r0);
+                __stcg(&vr->r1, r1);
+            } else if (keep) {
+                atomicOr(&ctl->flags, kFlagOverflow);
+            }
+        }
     }
     if (!grid_sync(ctl, target)) return false;
     // visit the kept tiles
@@ -425,13 +449,9 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
         if (gt == 0) {
             const int idx = first ? blockIdx.x * cta_groups + gi : groups + atomicAdd(vgrab, 1);
             if (idx < nv) {
-                const int g = __ldcg(P.vlist + idx);
-                unsigned key = kKeyInf;
-                if (ord.on) {
-                    key = __ldcg(kcur + g);
-                    __stcg(kcur + g, kKeyInf);
-                }
-                group_fetch(P, gc, g, key);
+                const VisitRec *vr = P.vlist + idx;
+                const int4 h = __ldcg(&vr->head);
+                group_set(gc, h.x, (unsigned)h.y, __ldcg(&vr->r0), __ldcg(&vr->r1));
             } else {
                 gc.tile = -1;
             }
