@@ -55,6 +55,7 @@ struct AdjParams {
     int *tile_rec;              // [n_tiles][8]: neighbours, instance, unused
     int *tstamp;
     int *list0, *list1;
+    VisitRec *vlist;            // tiles kept by the classification of a two-phase iteration
     T *phi_t, *tau_t, *lam_t, *r_t;
     Ctl *ctl;
     long long max_iters;
@@ -395,6 +396,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
             ctl->rcnt[(r + 2) % 3] = 0;
             ctl->rkmin[(r + 2) % 3] = kKeyInf;
             ctl->rgrab[(r + 2) % 3] = 0;
+            ctl->rvcnt[(r + 2) % 3] = 0;
+            ctl->rvgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
         const OrderCtx ord = order_begin(P.ordered, s_k, width);
@@ -402,26 +405,50 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
         const int *in = (r & 1) ? P.list1 : P.list0;
         int *out = (r & 1) ? P.list0 : P.list1;
         const int next_stamp = r + 2;
-        // groups take chunks of the list from a shared counter, classify a chunk
-        // with all their threads (deferred entries are listed again on the spot)
-        // and visit the kept tiles one by one
-        GroupQueue &q = gqs[gi];
-        int *grab = &ctl->rgrab[r % 3];
-        // the static first chunks cover the list: no grab from the shared counter
-        const bool static_only = (long long)gridDim.x * GG::NG * chunk >= n;
-        for (bool first = true;; first = false) {
-            if (!first && static_only) break;
-            if (gt == 0) {
-                q.n = 0;
-                q.base = grab_chunk(grab, first, blockIdx.x * GG::NG + gi, gridDim.x * GG::NG, chunk);
-            }
+        // Visit of tile g (its neighbours in s_nb[gi]) and the listing of the neighbour
+        // tiles across faces where lambda changed.
+        auto visit = [&](int g) {
+            int nb[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
+            unsigned mine;
+            bool changed;
+            const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
+            if (gt == 0) { tiles++; sweeps += s; atomicAdd(&s_visits, 1); }
+#pragma unroll
+            for (int m = 0; m < GG::NPT; ++m)
+                if (mine >> m & 1) {
+                    const int fb = G::faces_of(GG::node(gt, m));
+                    if (fb) atomicOr(&s_fmask[gi], fb);
+                }
             group_sync(bid, GG::GT);
-            const int base = q.base;
-            if (base >= n) break;                          // group-uniform
-            {
-                const int e = base + gt;
-                const bool valid = gt < chunk && e < n;
+            if (gt < 32) {
+                const int fm = s_fmask[gi];
+                int cand = -1;
+                if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
+                if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
+                const unsigned kc = (ord.on && cand >= 0) ? __ldg(P.tkey + cand) : kKeyInf;
+                const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
+                warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
+            }
+            group_sync(bid, GG::GT);                       // the visit is done with s_nb, s_fmask and sm
+        };
+        if ((r > 0 ? s_p : n) > groups) {
+            // more visits expected than groups: two phases split by a grid barrier (as the
+            // forward's group_pass_split): every thread classifies list entries, a kept tile
+            // goes to the visit list with its neighbours; then the groups take one visit at a time
+            const int lane = threadIdx.x & 31;
+            const int nthreads = gridDim.x * blockDim.x;
+            int *vcnt = &ctl->rvcnt[r % 3];
+            for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
+                const int e = e0 + lane;
+                const bool valid = e < n;
                 const int g = valid ? __ldcg(in + e) : -1;
+                int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+                if (valid) {
+                    r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_rec + 8 * g));
+                    r1 = __ldcg(reinterpret_cast<const int4 *>(P.tile_rec + 8 * g + 4));
+                }
                 const unsigned key = valid && ord.on ? __ldg(P.tkey + g) : kKeyInf;
                 const bool defer = valid && ord.on && !order_visit(ord, key);
                 bool want = false;
@@ -430,42 +457,88 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
                     deferred++;
                 }
                 warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, ord.on ? &ctl->rkmin[nslot] : nullptr, key);
-                if (valid && !defer) q.tile[atomicAdd(&q.n, 1)] = g;
-            }
-            group_sync(bid, GG::GT);
-            const int qn = q.n;
-            for (int qi = 0; qi < qn; ++qi) {
-                const int g = q.tile[qi];
-                if (gt == 0) {
-#pragma unroll
-                    for (int f = 0; f < 6; ++f) s_nb[gi][f] = __ldcg(P.tile_rec + 8 * g + f);
-                    s_fmask[gi] = 0;
-                }
-                group_sync(bid, GG::GT);
-                int nb[6];
-#pragma unroll
-                for (int f = 0; f < 6; ++f) nb[f] = s_nb[gi][f];
-                unsigned mine;
-                bool changed;
-                const int s = adj_visit<T, BX, BY, BZ>(P, sm, nb, g, gt, bid, mine, changed);
-                if (gt == 0) { tiles++; sweeps += s; atomicAdd(&s_visits, 1); }
-#pragma unroll
-                for (int m = 0; m < GG::NPT; ++m)
-                    if (mine >> m & 1) {
-                        const int fb = G::faces_of(GG::node(gt, m));
-                        if (fb) atomicOr(&s_fmask[gi], fb);
+                const bool keep = valid && !defer;
+                const unsigned m = __ballot_sync(kFull, keep);
+                if (m) {
+                    int base = 0;
+                    if (lane == __ffs(m) - 1) base = atomicAdd(vcnt, __popc(m));
+                    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+                    const int pos = base + __popc(m & ((1u << lane) - 1));
+                    if (keep && pos < P.n_tiles) {
+                        VisitRec *vr = P.vlist + pos;
+                        __stcg(&vr->head, make_int4(g, 0, 0, 0));
+                        __stcg(&vr->r0, r0);
+                        __stcg(&vr->r1, r1);
+                    } else if (keep) {
+                        atomicOr(&ctl->flags, kFlagOverflow);
                     }
-                group_sync(bid, GG::GT);
-                if (gt < 32) {
-                    const int fm = s_fmask[gi];
-                    int cand = -1;
-                    if (gt < 6 && (fm >> gt & 1) && (unsigned)nb[gt] < (unsigned)P.n_tiles) cand = nb[gt];
-                    if (gt == 6 && changed && s >= P.max_sweeps) cand = g;
-                    const unsigned kc = (ord.on && cand >= 0) ? __ldg(P.tkey + cand) : kKeyInf;
-                    const bool want = cand >= 0 && atomicExch(P.tstamp + cand, next_stamp) != next_stamp;
-                    warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, cand, ord.on ? &ctl->rkmin[nslot] : nullptr, kc);
                 }
-                group_sync(bid, GG::GT);                   // the visit is done with s_nb, s_fmask and sm
+            }
+            if (!grid_sync(ctl, target)) break;
+            const int nv = min(ld_volatile(vcnt), P.n_tiles);
+            __shared__ int s_tile[GG::NG];
+            for (bool first = true;; first = false) {
+                if (gt == 0) {
+                    const int idx = first ? blockIdx.x * GG::NG + gi : groups + atomicAdd(&ctl->rvgrab[r % 3], 1);
+                    int g = -1;
+                    if (idx < nv) {
+                        const VisitRec *vr = P.vlist + idx;
+                        g = __ldcg(&vr->head).x;
+                        const int4 a = __ldcg(&vr->r0), b = __ldcg(&vr->r1);
+                        s_nb[gi][0] = a.x; s_nb[gi][1] = a.y; s_nb[gi][2] = a.z; s_nb[gi][3] = a.w;
+                        s_nb[gi][4] = b.x; s_nb[gi][5] = b.y;
+                        s_fmask[gi] = 0;
+                    }
+                    s_tile[gi] = g;
+                }
+                group_sync(bid, GG::GT);
+                const int g = s_tile[gi];
+                if (g < 0) break;                          // group-uniform
+                visit(g);
+            }
+        } else {
+            // groups take chunks of the list from a shared counter, classify a chunk
+            // with all their threads (deferred entries are listed again on the spot)
+            // and visit the kept tiles one by one
+            GroupQueue &q = gqs[gi];
+            int *grab = &ctl->rgrab[r % 3];
+            // the static first chunks cover the list: no grab from the shared counter
+            const bool static_only = (long long)gridDim.x * GG::NG * chunk >= n;
+            for (bool first = true;; first = false) {
+                if (!first && static_only) break;
+                if (gt == 0) {
+                    q.n = 0;
+                    q.base = grab_chunk(grab, first, blockIdx.x * GG::NG + gi, gridDim.x * GG::NG, chunk);
+                }
+                group_sync(bid, GG::GT);
+                const int base = q.base;
+                if (base >= n) break;                          // group-uniform
+                {
+                    const int e = base + gt;
+                    const bool valid = gt < chunk && e < n;
+                    const int g = valid ? __ldcg(in + e) : -1;
+                    const unsigned key = valid && ord.on ? __ldg(P.tkey + g) : kKeyInf;
+                    const bool defer = valid && ord.on && !order_visit(ord, key);
+                    bool want = false;
+                    if (defer) {                               // deferred: listed again, not visited
+                        want = atomicExch(P.tstamp + g, next_stamp) != next_stamp;
+                        deferred++;
+                    }
+                    warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, ord.on ? &ctl->rkmin[nslot] : nullptr, key);
+                    if (valid && !defer) q.tile[atomicAdd(&q.n, 1)] = g;
+                }
+                group_sync(bid, GG::GT);
+                const int qn = q.n;
+                for (int qi = 0; qi < qn; ++qi) {
+                    const int g = q.tile[qi];
+                    if (gt == 0) {
+#pragma unroll
+                        for (int f = 0; f < 6; ++f) s_nb[gi][f] = __ldcg(P.tile_rec + 8 * g + f);
+                        s_fmask[gi] = 0;
+                    }
+                    group_sync(bid, GG::GT);
+                    visit(g);
+                }
             }
         }
         __syncthreads();

@@ -524,7 +524,7 @@ int solve_impl(int64_t B, const eik_grid *grids, const void *F, const int64_t *F
 
 // ---------------------------------------------------------------- adjoint
 struct AdjLayout {
-    size_t ctl, desc, inst_scale, tile_rec, tstamp, tkey, list0, list1, phi_t, tau_t, lam_t, r_t, total;
+    size_t ctl, desc, inst_scale, tile_rec, tstamp, tkey, list0, list1, vlist, phi_t, tau_t, lam_t, r_t, total;
     long long n_tiles;
     long long n_acc_tiles;        // tiles of the distinct gradient blocks
     std::vector<InstDesc> desc_host;
@@ -554,6 +554,7 @@ bool make_adj_layout(int64_t B, const eik_grid *grids, const Opts &o, AdjLayout 
     L.tkey = take(4 * (size_t)tiles);
     L.list0 = take(4 * (size_t)tiles);
     L.list1 = take(4 * (size_t)tiles);
+    L.vlist = take(sizeof(VisitRec) * (size_t)tiles);
     L.phi_t = take(esz * (size_t)(tiles * V));
     L.tau_t = take(esz * (size_t)(tiles * V));
     L.lam_t = take(esz * (size_t)(tiles * V));
@@ -607,6 +608,7 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     P.tstamp = reinterpret_cast<int *>(ws + L.tstamp);
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
     P.list1 = reinterpret_cast<int *>(ws + L.list1);
+    P.vlist = reinterpret_cast<VisitRec *>(ws + L.vlist);
     P.phi_t = reinterpret_cast<T *>(ws + L.phi_t);
     P.tau_t = reinterpret_cast<T *>(ws + L.tau_t);
     P.lam_t = reinterpret_cast<T *>(ws + L.lam_t);
