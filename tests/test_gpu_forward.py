@@ -241,6 +241,27 @@ def test_full_oscillating_256_fp32():
     print("oscillating_3d_256 max rel err", err, st)
 
 
+def test_many_fronts_two_phase_iterations():
+    """A 160^3 oscillating speed with 24 sources: iterations with more visits than
+    thread groups (the two-phase classify-then-visit iterations) occur, and the
+    result matches the oracle node for node."""
+    torch = _torch()
+    from paper_2106_15869_b300 import api
+    base = W.oscillating_3d(160)
+    rng = np.random.default_rng(7)
+    idx = np.unique(rng.integers(0, base.F.size, size=24)).astype(np.int64)
+    inst = W.Instance("osc160_multi", base.F, base.h, idx, np.zeros(idx.size))
+    F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
+    with api.Trace() as tr:
+        phi, st = api.solve(F, inst.src_idx, inst.h, return_stats=True)
+    assert st["status"] == 0, st
+    visits = tr.records[1:, 3]
+    groups = 3 * torch.cuda.get_device_properties(0).multi_processor_count   # 256-thread groups launched
+    big = visits > groups
+    assert np.any(big[:-1] & big[1:]), visits.max()    # an iteration after one with more visits than groups
+    assert_parity(phi.cpu().double().numpy(), oracle_phi(inst, "fp32"), TOL32)
+
+
 # ------------------------------------------------------------------ asynchronous schedule
 @pytest.mark.parametrize("seed", range(12))
 def test_async_random_small_grids(seed):
