@@ -457,22 +457,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
                     deferred++;
                 }
                 warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, ord.on ? &ctl->rkmin[nslot] : nullptr, key);
-                const bool keep = valid && !defer;
-                const unsigned m = __ballot_sync(kFull, keep);
-                if (m) {
-                    int base = 0;
-                    if (lane == __ffs(m) - 1) base = atomicAdd(vcnt, __popc(m));
-                    base = __shfl_sync(kFull, base, __ffs(m) - 1);
-                    const int pos = base + __popc(m & ((1u << lane) - 1));
-                    if (keep && pos < P.n_tiles) {
-                        VisitRec *vr = P.vlist + pos;
-                        __stcg(&vr->head, make_int4(g, 0, 0, 0));
-                        __stcg(&vr->r0, r0);
-                        __stcg(&vr->r1, r1);
-                    } else if (keep) {
-                        atomicOr(&ctl->flags, kFlagOverflow);
-                    }
-                }
+                push_visit(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g, key, r0, r1);
             }
             if (!grid_sync(ctl, target)) break;
             const int nv = min(ld_volatile(vcnt), P.n_tiles);

@@ -364,6 +364,28 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
     }
 }
 
+// Warp-aggregated append of kept tiles to the visit list of a two-phase
+// iteration, each with its key and record (every lane of the warp calls it).
+__device__ __forceinline__ void push_visit(Ctl *ctl, int *vcnt, VisitRec *vlist, int cap, bool keep, int g,
+                                           unsigned key, int4 r0, int4 r1) {
+    const unsigned m = __ballot_sync(kFull, keep);
+    if (!m) return;
+    const int lane = lane_id(), leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(vcnt, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (!keep) return;
+    const int pos = base + __popc(m & ((1u << lane) - 1));
+    if (pos < cap) {
+        VisitRec *vr = vlist + pos;
+        __stcg(&vr->head, make_int4(g, (int)key, 0, 0));
+        __stcg(&vr->r0, r0);
+        __stcg(&vr->r1, r1);
+    } else {
+        atomicOr(&ctl->flags, kFlagOverflow);
+    }
+}
+
 // An iteration of the latency-only kernel with more visits expected than
 // thread groups, in two phases split by a grid barrier.  First every thread
 // of the launch classifies list entries (a deferred entry is listed again on
@@ -395,7 +417,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     n = min(n, P.n_tiles);
     // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the
     // pushes); a kept tile goes to the visit list with its key and record
-    const int lane = threadIdx.x & 31;
+    const int lane = lane_id();
     const int nthreads = gridDim.x * blockDim.x;
     for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
         const int e = e0 + lane;
@@ -419,22 +441,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
             st_def++;
         }
         warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
-        const bool keep = valid && !defer;
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (m) {
-            int base = 0;
-            if (lane == __ffs(m) - 1) base = atomicAdd(vcnt, __popc(m));
-            base = __shfl_sync(kFull, base, __ffs(m) - 1);
-            const int pos = base + __popc(m & ((1u << lane) - 1));
-            if (keep && pos < P.n_tiles) {
-                VisitRec *vr = P.vlist + pos;
-                __stcg(&vr->head, make_int4(g, (int)key, 0, 0));
-                __stcg(&vr->r0, r0);
-                __stcg(&vr->r1, r1);
-            } else if (keep) {
-                atomicOr(&ctl->flags, kFlagOverflow);
-            }
-        }
+        push_visit(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g, key, r0, r1);
     }
     if (!grid_sync(ctl, target)) return false;
     // visit the kept tiles
