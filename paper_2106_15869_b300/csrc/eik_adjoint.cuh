@@ -311,6 +311,11 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             if (hi1 < INF && pj <= hi2 && hi1 > pj) w[m][2 * ax + 1] = T(2) * (hi1 - pj);
         }
     }
+    // 1 / J_jj once per visit: a sweep multiplies (the FP32 division in every sweep made the
+    // whole adjoint 1.26x slower on the 192^3 tomography batch)
+    T rJ[NPT];
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) rJ[m] = J[m] > T(0) ? T(1) / J[m] : T(0);
     // Sweeps on lambda until no change; sources and nodes with J == 0 keep
     // lambda.  A thread relaxes its z segment in descending z: lambda flows
     // toward lower phi, most often up the grid from receivers below the
@@ -323,7 +328,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
     for (;;) {
         unsigned ch = 0;
         auto relax = [&](int m) {
-            if (!(J[m] > T(0))) return;
+            if (!(rJ[m] > T(0))) return;
             const int c = G::sidx(x[m], y[m], z[m]);
             T acc = rr[m];
             acc += w[m][0] * sm.lam[c - 1];
@@ -335,7 +340,7 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
             const T lzhi = (GG::ZSEG && m + 1 < NPT) ? lam[m + 1 < NPT ? m + 1 : m] : sm.lam[c + G::SX * G::SY];
             acc += w[m][4] * lzlo;
             acc += w[m][5] * lzhi;
-            const T nl = acc / J[m];
+            const T nl = acc * rJ[m];
             if (nl != lam[m]) { lam[m] = nl; sm.lam[c] = nl; ch |= 1u << m; }
         };
 #pragma unroll
