@@ -553,13 +553,13 @@ __global__ void __launch_bounds__(kSpanThreads) k_adj_output(AdjParams<T> P) {
     using G = TileGeom<BX, BY, BZ>;
     constexpr int PER = kSpan * G::V / kSpanThreads;
     __shared__ TileSpan<BX, BY, BZ> sp;
-    __shared__ int s_cur[kSpan];                 // instance of each tile's chain being added (-1: done)
     for (long long a0 = (long long)blockIdx.x * kSpan; a0 < P.n_acc_tiles; a0 += (long long)gridDim.x * kSpan) {
-        if (threadIdx.x < kSpan) {
-            sp.fill(P.desc, P.B, P.n_acc_tiles, a0, threadIdx.x, true);
-            s_cur[threadIdx.x] = a0 + threadIdx.x < P.n_acc_tiles ? sp.inst[threadIdx.x] : -1;
-        }
+        if (threadIdx.x < kSpan) sp.fill(P.desc, P.B, P.n_acc_tiles, a0, threadIdx.x, true);
         __syncthreads();
+        // instance of each tile's chain being added (-1: done); every thread walks the chains itself
+        int bt[kSpan];
+#pragma unroll
+        for (int t = 0; t < kSpan; ++t) bt[t] = a0 + t < P.n_acc_tiles ? sp.inst[t] : -1;
         T sum[PER];
         bool any[PER];
 #pragma unroll
@@ -567,30 +567,35 @@ __global__ void __launch_bounds__(kSpanThreads) k_adj_output(AdjParams<T> P) {
         for (;;) {
             bool live = false;
 #pragma unroll
-            for (int t = 0; t < kSpan; ++t) live |= s_cur[t] >= 0;
-            if (!live) break;                                       // uniform: every thread read the same s_cur
-            T lam[PER], tau[PER], phi[PER], h2[PER];
+            for (int t = 0; t < kSpan; ++t) live |= bt[t] >= 0;
+            if (!live) break;                                       // uniform: every thread walks the same chains
+            T lam[PER], h2[PER];
+            long long e[PER];
 #pragma unroll
             for (int m = 0; m < PER; ++m) {
                 const int r = threadIdx.x + m * kSpanThreads, t = r / G::V, q = r % G::V;
-                const int b = s_cur[t];
-                lam[m] = T(0); tau[m] = T(-1); phi[m] = Num<T>::inf(); h2[m] = T(0);
+                int b = bt[0];
+#pragma unroll
+                for (int u = 1; u < kSpan; ++u) b = t == u ? bt[u] : b;
+                lam[m] = T(0); h2[m] = T(0); e[m] = -1;
                 if (b < 0) continue;
-                const long long e = (P.desc[b].tile_base + sp.l[t]) * G::V + q;
-                lam[m] = __ldcs(P.lam_t + e);
-                tau[m] = __ldcs(P.tau_t + e);
-                phi[m] = __ldcs(P.phi_t + e);
+                e[m] = (P.desc[b].tile_base + sp.l[t]) * G::V + q;
+                lam[m] = __ldcs(P.lam_t + e[m]);
                 h2[m] = T(2) * T(P.desc[b].h);
             }
+            // lambda != 0 only at non-source nodes with finite phi and tau (the visits keep
+            // lambda = 0 elsewhere): tau is read only there
 #pragma unroll
             for (int m = 0; m < PER; ++m) {
-                if (lam[m] == T(0) || tau[m] < T(0) || !(tau[m] < Num<T>::inf()) || !(phi[m] < Num<T>::inf())) continue;
-                sum[m] += h2[m] * tau[m] * lam[m];
+                if (lam[m] == T(0)) continue;
+                const T tau = __ldcs(P.tau_t + e[m]);
+                if (tau < T(0) || !(tau < Num<T>::inf())) continue;
+                sum[m] += h2[m] * tau * lam[m];
                 any[m] = true;
             }
-            __syncthreads();                                        // s_cur read by all
-            if (threadIdx.x < kSpan && s_cur[threadIdx.x] >= 0) s_cur[threadIdx.x] = P.desc[s_cur[threadIdx.x]].acc_next;
-            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < kSpan; ++t)
+                if (bt[t] >= 0) bt[t] = P.desc[bt[t]].acc_next;
         }
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
