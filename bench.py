@@ -49,7 +49,7 @@ LAUNCHES_PER_SOLVE = 7
 # reported only for those options and while the kernel sources still hash to the captured
 # version (else null).
 MEASURED_TRAFFIC = {
-    "oscillating_256": {"hash": "bbdb05a760702c9f", "bytes": 354566656 + 87154688},
+    "oscillating_256": {"hash": "bf0db4ccf9e1ae4f", "bytes": 354566656 + 87154688},
 }
 
 
@@ -65,12 +65,17 @@ PAPER_TIMES_S = {
 }
 
 
+# the sources the forward solve's kernels (and their launch) are built from; the adjoint and
+# back-trace headers are left out, so that changing them keeps the captured forward counters
+FORWARD_SOURCES = ("eik_api.cu", "eik_async.cuh", "eik_common.cuh", "eik_forward.cuh", "eik_group.cuh",
+                   "eik_kernels.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_15869_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in FORWARD_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
