@@ -194,7 +194,8 @@ def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances
     device, one dtype); phis: the forward solutions (checkpoints); rs: dL/dphi
     per instance (same shapes).  With shared_F every instance uses the first
     F; with sum_instances the gradients of all instances are accumulated into
-    one tensor shaped like the first F (e.g. many shots on one slowness model).
+    one tensor shaped like the first F (e.g. many shots on one slowness model),
+    summed in instance order, so that repeated calls are bit-identical.
     Returns a list of gradients, or one tensor with sum_instances.
     """
     if not problems:
