@@ -352,6 +352,7 @@ def run_ours(args, ws, rank, local):
         if len(insts) == 1:
             line["fim_vs_ifim"] = bench_methods(args, insts[0], F, idx, val, phi, wsp, flush_buf)
             line["backtrace"] = bench_backtrace(args, insts[0], F, idx, val, phi, wsp, flush_buf)
+            line["unequal_spacings"] = bench_spacings(args, insts[0], F, idx, val, phi, wsp, flush_buf)
         line["batched"] = bench_batched(args, dev, wsp, flush_buf)
         line["adjoint"] = bench_adjoint(args, dev, wsp, flush_buf)
         line["paper_examples"] = bench_paper_examples(args, dev, wsp, flush_buf)
@@ -404,6 +405,23 @@ def bench_methods(args, inst, F, idx, val, phi, wsp, flush_buf):
                      "iterations": st["iters_update"] + st["iters_remedy"],
                      "tile_visits": st["tiles_update"] + st["tiles_remedy"], "sweeps": st["sweeps"]}
     out["fim_speedup_over_ifim"] = out["ifim"]["ms"] / out["fim"]["ms"]
+    return out
+
+
+def bench_spacings(args, inst, F, idx, val, phi, wsp, flush_buf):
+    """The same speeds on a stretched grid, spacings (h, 1.25 h, 2 h) (eq. 6 with unequal
+    spacings, the 3D form of Alg 1.2), against equal spacings h."""
+    from paper_2106_15869_b300 import api
+    out = {}
+    for name, h in (("equal", inst.h), ("unequal", (inst.h, 1.25 * inst.h, 2.0 * inst.h))):
+        run = lambda: api.solve(F, idx, h, val, workspace=wsp, out=phi)
+        run()
+        ms = _timed(run, flush_buf, 5)
+        _, st = api.solve(F, idx, h, val, workspace=wsp, out=phi, return_stats=True)
+        out[name] = {"spacings": h if isinstance(h, tuple) else (h, h, h), "ms": ms,
+                     "nodes_per_s": inst.n_nodes / (ms / 1e3), "sweeps": st["sweeps"],
+                     "tile_visits": st["tiles_update"] + st["tiles_remedy"]}
+    out["unequal_over_equal"] = out["unequal"]["ms"] / out["equal"]["ms"]
     return out
 
 

@@ -312,6 +312,10 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.mt.cy = (T)L.cy;
     P.mt.cz = (T)L.cz;
     P.mt.aniso = L.aniso ? 1 : 0;
+    P.mt.r_xy = (T)(1.0 / (1.0 + L.cy));
+    P.mt.r_xz = (T)(1.0 / (1.0 + L.cz));
+    P.mt.r_yz = (T)(1.0 / (L.cy + L.cz));
+    P.mt.r_xyz = (T)(1.0 / (1.0 + L.cy + L.cz));
     P.one_visit = o.converge == EIK_CONVERGE_SWEEP ? 1 : 0;
     P.max_sweeps = 4 * (BX + BY + BZ) + 8;
     P.F = static_cast<const T *>(F);

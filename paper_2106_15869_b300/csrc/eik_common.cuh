@@ -213,6 +213,7 @@ template <class T>
 struct Metric {
     T cy, cz;     // (dx / dy)^2, (dx / dz)^2
     int aniso;    // 0: equal spacings, the isotropic cascade
+    T r_xy, r_xz, r_yz, r_xyz;   // 1 / (1 + cy), 1 / (1 + cz), 1 / (cy + cz), 1 / (1 + cy + cz)
 };
 
 // compare-exchange of (minimum, weight) pairs by minimum
@@ -242,32 +243,36 @@ __device__ __forceinline__ T local_solve_w(T ax, T ay, T az, T tau, T cy, T cz) 
 }
 
 // FP32 sweep form of local_solve_w: the three candidate roots at once, then
-// the selection (as local_solve_fast).
-__device__ __forceinline__ float local_solve_fast_w(float ax, float ay, float az, float tau, float cy, float cz) {
-    float a1 = ax, c1 = 1.0f, a2 = ay, c2 = cy, a3 = az, c3 = cz;
+// the selection (as local_solve_fast).  The weight sums C2 and C3 take one of
+// four values per call, whose reciprocals the call provides: the two-sided sum
+// is fixed by the weight left out (c3), so no root divides.
+__device__ __forceinline__ float local_solve_fast_w(float ax, float ay, float az, float tau, const Metric<float> &mt) {
+    float a1 = ax, c1 = 1.0f, a2 = ay, c2 = mt.cy, a3 = az, c3 = mt.cz;
     cx_pair(a1, c1, a2, c2);
     cx_pair(a2, c2, a3, c3);
     cx_pair(a1, c1, a2, c2);
+    const float rC2 = c3 == 1.0f ? mt.r_yz : (c3 == mt.cy ? mt.r_xz : mt.r_xy);
     const float t2 = tau * tau, C2 = c1 + c2, C3 = C2 + c3;
     const float d2 = a2 - a1, d3 = a3 - a1, d32 = d3 - d2;
     const float u1 = a1 + tau * rsqrtf(c1);
-    const float u2 = a1 + (c2 * d2 + sqrt_approx(C2 * t2 - c1 * c2 * d2 * d2)) / C2;
+    const float u2 = a1 + (c2 * d2 + sqrt_approx(C2 * t2 - c1 * c2 * d2 * d2)) * rC2;
     const float u3 =
-        a1 + (c2 * d2 + c3 * d3 + sqrt_approx(C3 * t2 - (c1 * c2 * d2 * d2 + c1 * c3 * d3 * d3 + c2 * c3 * d32 * d32))) / C3;
+        a1 + (c2 * d2 + c3 * d3 + sqrt_approx(C3 * t2 - (c1 * c2 * d2 * d2 + c1 * c3 * d3 * d3 + c2 * c3 * d32 * d32))) *
+                 mt.r_xyz;
     return u1 <= a2 ? u1 : (u2 <= a3 ? u2 : u3);
 }
 
-__device__ __forceinline__ float sweep_solve_w(float ax, float ay, float az, float tau, float cy, float cz) {
-    return local_solve_fast_w(ax, ay, az, tau, cy, cz);
+__device__ __forceinline__ float sweep_solve_w(float ax, float ay, float az, float tau, const Metric<float> &mt) {
+    return local_solve_fast_w(ax, ay, az, tau, mt);
 }
-__device__ __forceinline__ double sweep_solve_w(double ax, double ay, double az, double tau, double cy, double cz) {
-    return local_solve_w<double>(ax, ay, az, tau, cy, cz);
+__device__ __forceinline__ double sweep_solve_w(double ax, double ay, double az, double tau, const Metric<double> &mt) {
+    return local_solve_w<double>(ax, ay, az, tau, mt.cy, mt.cz);
 }
 
 // The root every relaxation uses: isotropic cascade, or the weighted one.
 template <class T>
 __device__ __forceinline__ T node_solve(T ax, T ay, T az, T tau, const Metric<T> &mt) {
-    return mt.aniso ? sweep_solve_w(ax, ay, az, tau, mt.cy, mt.cz) : sweep_solve(ax, ay, az, tau);
+    return mt.aniso ? sweep_solve_w(ax, ay, az, tau, mt) : sweep_solve(ax, ay, az, tau);
 }
 
 // Device-wide barrier for a cooperative launch.  Every wait is bounded by
