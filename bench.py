@@ -55,7 +55,8 @@ MEASURED_TRAFFIC = {
 
 # The paper's own timings (seconds on an NVIDIA Tesla P100; Tables 1, 2, 3 and 5,
 # Sec. 4.1) of its GPU FIM and iFIM for Examples 1, 2, 3 and 5 at N^2 nodes --
-# context for the B300 times of the same examples, not a target.
+# context for the B300 times of the same examples, not a target.  As printed, the FIM
+# rows of Tables 3 and 5 share their first four entries; they are kept as printed.
 PAPER_SIZES = (200, 500, 1000, 2000, 4000)
 PAPER_TIMES_S = {
     1: {"fim": (0.00164, 0.00428, 0.08834, 0.32604, 1.67655), "ifim": (0.00141, 0.00384, 0.03721, 0.11642, 0.80981)},
