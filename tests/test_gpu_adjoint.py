@@ -182,3 +182,52 @@ def test_shared_gradient_block_is_deterministic(dtype):
     tol = 1e-12 if dtype == "fp64" else 1e-5
     assert float((runs[0].double() - want).abs().max()) <= tol * float(want.abs().max())
     assert float(want.abs().max()) > 0
+
+
+def test_interleaved_gradient_blocks_through_the_c_abi():
+    """Four instances writing two gradient blocks in the order A, B, A, B (offsets
+    0, N, 0, N): each block holds the sum of its two instances' gradients, and a
+    repeated call gives the same bits."""
+    import ctypes
+    torch = _torch()
+    from paper_2106_15869_b300 import _lib, api
+    w = W.tomography_3d(32, src_lattice=(6, 16, 26), rec_count=4, rec_start=4, rec_step=8)
+    F = torch.as_tensor(1.0 / w["s_true"], dtype=torch.float64).cuda()
+    shots = [[int(s)] for s in w["sources"][:4]]
+    probs = [(F, sh, w["h"]) for sh in shots]
+    phis = api.solve_batched(probs, shared_F=True)
+    rec = torch.as_tensor(w["receivers"]).cuda()
+    rs = []
+    for ph in phis:
+        r = torch.zeros_like(ph).reshape(-1)
+        r[rec] = ph.reshape(-1)[rec]
+        rs.append(r.view(ph.shape))
+    sep = api.adjoint_batched(probs, phis, rs, shared_F=True)
+    want = [(sep[0] + sep[2]).reshape(-1), (sep[1] + sep[3]).reshape(-1)]
+    N = F.numel()
+    lib = _lib.load()
+    dims = [(32, 32, 32, w["h"])] * 4
+    grids = _lib.grids_array(dims)
+    opt = _lib.make_options(precision="fp64")
+    nbytes = lib.eik_adjoint_workspace_size_batched(4, grids, ctypes.byref(opt))
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    phi_packed = torch.cat([p.reshape(-1) for p in phis])
+    r_packed = torch.cat([r.reshape(-1) for r in rs])
+    src = torch.as_tensor([s[0] for s in shots], dtype=torch.int64).cuda()
+    off = _lib.i64_array([0, N, 2 * N, 3 * N])
+    outs = []
+    for _ in range(2):
+        g = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+        rc = lib.eik_adjoint_batched(4, grids, F.data_ptr(), _lib.i64_array([0, 0, 0, 0]), phi_packed.data_ptr(), off,
+                                     src.data_ptr(), _lib.i64_array([0, 1, 2, 3, 4]), r_packed.data_ptr(),
+                                     g.data_ptr(), _lib.i64_array([0, N, 0, N]), base, nbytes, None,
+                                     ctypes.byref(opt), None)
+        _lib.check(rc)
+        torch.cuda.synchronize()
+        outs.append(g)
+    assert torch.equal(outs[0], outs[1])
+    for k in range(2):
+        got = outs[0][k * N:(k + 1) * N]
+        assert float((got - want[k]).abs().max()) <= 1e-12 * float(want[k].abs().max())
+    assert float(want[0].abs().max()) > 0 and float(want[1].abs().max()) > 0
