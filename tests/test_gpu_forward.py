@@ -226,6 +226,24 @@ def test_batched_shared_speed_many_sources():
         assert_parity(o.cpu().numpy(), ref, TOL64)
 
 
+def test_batched_many_small_instances():
+    """1500 small 3D instances (8..20 nodes per edge, one to four sources each) in one
+    launch: lists far longer than the thread groups (two-phase iterations over many
+    instances); every instance matches the oracle."""
+    from paper_2106_15869_b300 import api
+    torch = _torch()
+    rng = np.random.default_rng(31)
+    insts = []
+    for q in range(1500):
+        d = tuple(int(v) for v in rng.integers(8, 21, size=3))
+        insts.append(W.random_small(1000 + q, dims=d, three_d=True))
+    probs = [(torch.as_tensor(i.F, dtype=torch.float32).cuda(), i.src_idx, i.h, i.src_val) for i in insts]
+    outs, st = api.solve_batched(probs, return_stats=True)
+    assert st["status"] == 0, st
+    for i, o in zip(insts, outs):
+        assert_parity(o.cpu().double().numpy(), oracle_phi(i, "fp32"), TOL32)
+
+
 # ------------------------------------------------------------------ full-size workloads
 def test_full_point_source_2d_128_config():
     inst = W.point_source_2d(128, (64, 64))
