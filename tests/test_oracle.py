@@ -465,3 +465,111 @@ def test_backtrace_length_close_to_the_straight_segment():
         p = np.stack([path % n, (path // n) % n, path // (n * n)], 1).astype(float)
         L = np.sum(np.linalg.norm(np.diff(p, axis=0), axis=1))
         assert np.linalg.norm(p[0]) - 1e-12 <= L <= 1.2 * np.linalg.norm(p[0]) + 1e-12
+
+
+# ---------------------------------------------------------------- residual checker (eq. 6), hand-worked values
+def _residual_case(case):
+    """phi map, speeds, spacing and sources of a case of tests/golden/residual.txt."""
+    if case == "R1":
+        phi = np.array([0.0, 1.0, 2.25, 3.0, 4.0]).reshape(1, 1, 5)
+        return phi, np.ones_like(phi), 1.0, [0]
+    if case == "R2":
+        phi = np.array([[0.0, 1.0, 2.0], [1.0, 1.5, 5.0]])
+        F = np.ones_like(phi)
+        F[1, 1] = 2.0
+        return phi, F, 1.0, [0]
+    if case == "R3":
+        phi = np.full((3, 3, 3), 10.0)
+        phi[1, 1, 1] = 2.0
+        phi[1, 1, 0], phi[1, 1, 2], phi[1, 0, 1], phi[0, 1, 1] = 1.0, 3.0, 1.25, 1.5
+        return phi, np.ones_like(phi), 0.5, [0]
+    raise KeyError(case)
+
+
+def _golden_text_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def test_residual_golden_hand_worked_values():
+    """eko_residual reports the eq.-(6) residual worked out by hand at every listed node
+    (tests/golden/residual.txt): a raised node on an exact 1D solution and its downstream
+    neighbour, a 2D map where the (.)^+ clamp drops upwind terms, a 3D node with three
+    upwind neighbours.  A residual that always returned 0, dropped the clamp, read a
+    transposed neighbour or ignored F fails one of them."""
+    rows = _golden_text_rows("residual.txt")
+    assert len(rows) >= 11
+    seen = set()
+    for case, nx, ny, nz, h, i, j, k, want in rows:
+        phi, F, hh, src = _residual_case(case)
+        assert phi.size == int(nx) * int(ny) * int(nz) and hh == float(h)
+        worst, res = oracle.residual(F, hh, src, phi, per_node=True)
+        flat = (int(k) * int(ny) + int(j)) * int(nx) + int(i)
+        assert res.reshape(-1)[flat] == float(want), (case, i, j, k, res.reshape(-1)[flat])
+        assert worst >= float(want)
+        seen.add(case)
+    assert seen == {"R1", "R2", "R3"}
+    # the maximum over the 1D line is the raised node
+    phi, F, hh, src = _residual_case("R1")
+    assert oracle.residual(F, hh, src, phi) == 0.5625
+
+
+def test_residual_single_defect_on_a_solution():
+    """On an FMM solution the residual is zero to rounding; raising one interior node by
+    delta makes exactly that node and the neighbours it feeds report nonzero residuals."""
+    inst = W.oscillating_3d(20)
+    phi = oracle.fmm(inst.F, inst.h, inst.src_idx, inst.src_val)
+    base, res0 = oracle.residual(inst.F, inst.h, inst.src_idx, phi, per_node=True)
+    assert base < 1e-12
+    p = (10 * 20 + 9) * 20 + 11
+    bad = phi.copy().reshape(-1)
+    bad[p] += 0.25 * inst.h
+    worst, res = oracle.residual(inst.F, inst.h, inst.src_idx, bad.reshape(phi.shape), per_node=True)
+    res = res.reshape(-1)
+    changed = set(np.flatnonzero(res > 1e-9).tolist())
+    nbrs = {p - 1, p + 1, p - 20, p + 20, p - 400, p + 400}
+    assert p in changed and changed <= nbrs | {p}
+    # at p itself: sum_d ((u + d - a_d)^+)^2 with the same minima, divided by tau^2
+    tau = inst.h / inst.F.reshape(-1)[p]
+    u = bad[p]
+    a = []
+    for lo, hi in ((p - 1, p + 1), (p - 20, p + 20), (p - 400, p + 400)):
+        a.append(min(bad[lo], bad[hi]))
+    want = abs(sum(max(u - v, 0.0) ** 2 for v in a) - tau * tau) / (tau * tau)
+    assert res[p] == pytest.approx(want, rel=1e-12)
+    assert worst == pytest.approx(max(res), rel=0)
+
+
+def test_residual_impassable_sources_and_unreachable():
+    """A finite value on an impassable node (F = 0) is an infinite residual; sources and
+    +inf (unreachable) nodes are not checked."""
+    phi = np.array([0.0, 1.0, 2.0, np.inf]).reshape(1, 1, 4)
+    F = np.array([1.0, 1.0, 0.0, 0.0]).reshape(1, 1, 4)
+    worst, res = oracle.residual(F, 1.0, [0], phi, per_node=True)
+    assert math.isinf(res.reshape(-1)[2]) and math.isinf(worst)
+    assert res.reshape(-1)[3] == 0.0 and res.reshape(-1)[1] == 0.0
+    # a source holding any value is exempt
+    phi2 = np.array([5.0, 1.0]).reshape(1, 1, 2)
+    assert oracle.residual(np.ones((1, 1, 2)), 1.0, [0, 1], phi2) == 0.0
+
+
+def test_backtrace_ties_go_to_the_lower_flat_index():
+    """Equal slopes to two lower neighbours: the oracle's path takes the lower flat index
+    (tests/golden/backtrace_ties.txt; the rule of Example 4's descent as read here)."""
+    rows = _golden_text_rows("backtrace_ties.txt")
+    assert len(rows) == 3
+    for row in rows:
+        case, start = row[0], int(row[1])
+        rest = row[2:]
+        path = [int(v) for v in rest if ":" not in v]
+        phi = np.full(9, 10.0)
+        for pair in (v for v in rest if ":" in v):
+            n, val = pair.split(":")
+            phi[int(n)] = float(val)
+        got = oracle.backtrace(phi.reshape(3, 3), 1.0, [start])[0]
+        assert got.tolist() == path, (case, got)
