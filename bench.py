@@ -2,15 +2,24 @@
 """Throughput of the improved-FIM Eikonal solve on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload oscillating_256|point_source_128|maze_512|lognormal_batch64]
+                    [--workload maze_512|oscillating_256|point_source_128|lognormal_batch64]
 
 One step = one complete solve (Steps 1-3 of Algorithm 2 and the output
-unpack) of the workload, inputs already resident in HBM.  The metric is
-converged grid nodes per second, FP32.  Each step's device time is measured
-with CUDA events on the solve's stream (first to last kernel); L2 is flushed
-between steps by a 256 MiB write outside the measured interval.  With N > 1
-(torchrun) every rank solves its own replica (weak scaling, no collective on
-the data path); value = nodes over all ranks / max over ranks of the time.
+unpack) of the workload, inputs already resident in HBM.  The default workload
+is the largest single grid: the 512^3 maze (134 M nodes, slabs of slow walls
+with one gap each, 4 sources).  The metric is converged grid nodes per second,
+FP32.  Each step's device time is measured with CUDA events that the library
+records on the solve's stream (first to last kernel); L2 is flushed between
+steps by a 256 MiB write outside the measured interval.  With N > 1 (torchrun)
+every rank solves its own replica (weak scaling, no collective on the data
+path); value = nodes over all ranks / max over ranks of the time.
+
+Beside the headline line's own roofline (the Step-2/3 loop kernel of the 512^3
+maze) the line carries the other forms, each with its roofline block: the
+64-instance lognormal batch on autotuned options, replayed from a CUDA graph;
+the 192^3 tomography (16 shots: forward, adjoint, forward + adjoint); the 256^3
+oscillating-speed grid; the paper's 2D examples; and the FIM of Sec. 2.3 on the
+headline grid.
 
 --impl reference times the FP64 CPU oracle (fast marching) on the host cores
 on a bounded sample of the same workload (rank 0 only).
@@ -39,18 +48,19 @@ LOOP_BYTES_PER_NODE = 20
 # whole step incl. layout conversion: F read, tau/phi brick writes (12 B),
 # the loop (20 B), unpack read + write (8 B)
 STEP_BYTES_PER_NODE = 40
+# the adjoint's loop kernel: phi, tau and r read once, lambda written once (16 B per node)
+ADJ_LOOP_BYTES_PER_NODE = 16
 FALLBACK_HBM_GBS = 6400.0
 # kernels of one default solve: k_write_desc, k_init, k_scale, k_tile_scale, k_sources,
 # k_persistent, k_unpack
 LAUNCHES_PER_SOLVE = 7
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_persistent launch with
-# the default options, from the ncu capture summarised in profiles/k_persistent_oscillating256.md;
-# reported only for those options and while the kernel sources still hash to the captured
-# version (else null).
-MEASURED_TRAFFIC = {
-    "oscillating_256": {"hash": "7d3bfa52392ab76f", "bytes": 351688448 + 85334272},
-}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the loop kernel
+# with the default options, from ncu captures of that kernel (summaries under profiles/);
+# reported only for those options and while the kernel sources hash to the captured version
+# (else null).  "scaled_from" names a smaller capture of the same recipe whose traffic was
+# scaled by the node count.
+MEASURED_TRAFFIC = {}
 
 
 # The paper's own timings (seconds on an NVIDIA Tesla P100; Tables 1, 2, 3 and 5,
@@ -70,12 +80,13 @@ PAPER_TIMES_S = {
 # back-trace headers are left out, so that changing them keeps the captured forward counters
 FORWARD_SOURCES = ("eik_api.cu", "eik_async.cuh", "eik_common.cuh", "eik_forward.cuh", "eik_group.cuh",
                    "eik_kernels.cuh")
+ADJOINT_SOURCES = FORWARD_SOURCES + ("eik_adjoint.cuh",)
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=FORWARD_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_15869_b300", "csrc")
-    for f in FORWARD_SOURCES:
+    for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -86,6 +97,24 @@ def measured_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def captured_traffic(key: str, files=FORWARD_SOURCES):
+    """Bytes per launch from MEASURED_TRAFFIC for `key`, or None when absent or stale."""
+    t = MEASURED_TRAFFIC.get(key)
+    if not t or t.get("hash") != kernel_source_hash(files):
+        return None
+    return t["bytes"]
+
+
+def roofline_block(kernel: str, bytes_per_node: float, nodes: int, loop_ms: float, traffic=None, **extra) -> dict:
+    """Roofline of one loop kernel: algorithmic bytes (bytes_per_node x nodes) over its
+    device time, against the measured HBM copy bandwidth."""
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_node * nodes / (loop_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_node": bytes_per_node, "nodes": nodes, "loop_ms": loop_ms, **extra}
 
 
 class ClockSampler:
@@ -178,15 +207,22 @@ def make_workload(name: str):
 
 
 def cpu_sample(name: str):
-    """Bounded sample of the workload for the oracle timing."""
+    """Bounded sample of the workload for the oracle timing (single-threaded fast marching)."""
     from paper_2106_15869_b300 import workloads as W
     if name == "oscillating_256":
         return W.oscillating_3d(256), "full 256^3 oscillating-speed grid, one FMM solve"
     if name == "point_source_128":
         return W.point_source_2d(128, (64, 64)), "full 128^2 grid"
     if name == "maze_512":
-        return W.maze_3d(192, n_slabs=6, gap=12), "192^3 maze built by the same recipe (6 slabs/axis)"
+        return W.maze_3d(192, n_slabs=6, gap=12), "192^3 maze built by the same recipe (6 slabs/axis, 12^2 gaps)"
     return W.lognormal_batch(4)[0], "first instance of the lognormal batch"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args, ws, rank):
@@ -217,10 +253,9 @@ def run_reference(args, ws, rank):
 
 
 def run_ours(args, ws, rank, local):
-    import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2106_15869_b300 import api, _lib
+    from paper_2106_15869_b300 import api
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -304,20 +339,16 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": n_nodes * ws / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(phi_h.numel() * 4),
                "ms_per_step": statistics.mean(e2e_ms)}
+        del F_h, phi_h
 
-    peak, peak_kind = measured_peaks()
-    achieved = LOOP_BYTES_PER_NODE * n_nodes / (loop_ms / 1e3) / 1e9
     src_hash = kernel_source_hash()
     # the captured traffic belongs to the default options only
     default_opts = (args.method == "ifim" and args.tile == "auto" and args.schedule == "auto"
                     and args.order == 0.0 and args.converge == "auto")
-    traffic = MEASURED_TRAFFIC.get(args.workload) if default_opts else None
-    traffic = traffic["bytes"] if traffic and traffic.get("hash") == src_hash else None
-    roofline = {"bound": "hbm", "kernel": "k_persistent (Steps 2-3)", "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_node": LOOP_BYTES_PER_NODE,
-                "loop_ms": loop_ms, "loop_share_of_step": loop_ms / ms_step,
-                "step_achieved_gbs": STEP_BYTES_PER_NODE * n_nodes / (ms_step / 1e3) / 1e9}
+    traffic = captured_traffic(args.workload) if default_opts else None
+    roofline = roofline_block("k_persistent (Steps 2-3)", LOOP_BYTES_PER_NODE, n_nodes, loop_ms, traffic,
+                              loop_share_of_step=loop_ms / ms_step,
+                              step_achieved_gbs=STEP_BYTES_PER_NODE * n_nodes / (ms_step / 1e3) / 1e9)
     s0 = stats[-1]
     # work of the loop: in-tile sweeps x nodes per tile, an upper bound of the local solves (a
     # latency-mode sweep solves every node of its tile; throughput-mode sweeps skip node slots
@@ -354,6 +385,9 @@ def run_ours(args, ws, rank, local):
             line["fim_vs_ifim"] = bench_methods(args, insts[0], F, idx, val, phi, wsp, flush_buf)
             line["backtrace"] = bench_backtrace(args, insts[0], F, idx, val, phi, wsp, flush_buf)
             line["unequal_spacings"] = bench_spacings(args, insts[0], F, idx, val, phi, wsp, flush_buf)
+            del F, phi
+        if args.workload != "oscillating_256":
+            line["oscillating_256"] = bench_single(dev, wsp, flush_buf, "oscillating_256")
         line["batched"] = bench_batched(args, dev, wsp, flush_buf)
         line["adjoint"] = bench_adjoint(args, dev, wsp, flush_buf)
         line["paper_examples"] = bench_paper_examples(args, dev, wsp, flush_buf)
@@ -367,6 +401,9 @@ def run_ours(args, ws, rank, local):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": inst_c.n_nodes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
+        if not args.no_extras:
+            line["batched"]["cpu_baseline"] = cpu_baseline_batch(8)
+            line["adjoint"]["cpu_baseline"] = cpu_baseline_tomography(8)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -400,9 +437,9 @@ def bench_methods(args, inst, F, idx, val, phi, wsp, flush_buf):
     for name, kw in (("ifim", dict(method="ifim")), ("fim", dict(method="fim", order=-1.0))):
         run = lambda: api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, **kw)
         run()
-        ms = _timed(run, flush_buf, 5)
+        ms = _timed(run, flush_buf, 3)
         _, st = api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, return_stats=True, **kw)
-        out[name] = {"ms": ms, "nodes_per_s": inst.n_nodes / (ms / 1e3),
+        out[name] = {"ms": ms, "nodes_per_s": inst.n_nodes / (ms / 1e3), "loop_ms": st["ms_loop"],
                      "iterations": st["iters_update"] + st["iters_remedy"],
                      "tile_visits": st["tiles_update"] + st["tiles_remedy"], "sweeps": st["sweeps"]}
     out["fim_speedup_over_ifim"] = out["ifim"]["ms"] / out["fim"]["ms"]
@@ -417,7 +454,7 @@ def bench_spacings(args, inst, F, idx, val, phi, wsp, flush_buf):
     for name, h in (("equal", inst.h), ("unequal", (inst.h, 1.25 * inst.h, 2.0 * inst.h))):
         run = lambda: api.solve(F, idx, h, val, workspace=wsp, out=phi)
         run()
-        ms = _timed(run, flush_buf, 5)
+        ms = _timed(run, flush_buf, 3)
         _, st = api.solve(F, idx, h, val, workspace=wsp, out=phi, return_stats=True)
         out[name] = {"spacings": h if isinstance(h, tuple) else (h, h, h), "ms": ms,
                      "nodes_per_s": inst.n_nodes / (ms / 1e3), "sweeps": st["sweeps"],
@@ -441,6 +478,32 @@ def bench_backtrace(args, inst, F, idx, val, phi, wsp, flush_buf):
     steps = int(length.clamp(min=0).sum().item())
     return {"paths": 4096, "max_len": max_len, "ms": ms, "path_nodes": steps,
             "path_nodes_per_s": steps / (ms / 1e3), "mean_length": steps / 4096}
+
+
+def bench_single(dev, wsp, flush_buf, name):
+    """A secondary single-grid workload with the default options: device time per solve and
+    the loop kernel's roofline."""
+    import torch
+    from paper_2106_15869_b300 import api
+    inst = make_workload(name)[0]
+    F = torch.as_tensor(inst.F, dtype=torch.float32).to(dev)
+    idx = torch.as_tensor(inst.src_idx).to(dev)
+    val = torch.as_tensor(inst.src_val, dtype=torch.float32).to(dev)
+    phi = torch.empty_like(F)
+    run = lambda: api.solve(F, idx, inst.h, val, workspace=wsp, out=phi, return_stats=True)
+    run()
+    loops, tots = [], []
+    for _ in range(5):
+        flush_buf.zero_()
+        _, st = run()
+        loops.append(st["ms_loop"])
+        tots.append(st["ms_total"])
+    loop_ms, ms = statistics.median(loops), statistics.median(tots)
+    return {"workload": name, "nodes": inst.n_nodes, "ms": ms, "nodes_per_s": inst.n_nodes / (ms / 1e3),
+            "solver_stats": {k: st[k] for k in ("iters_update", "iters_remedy", "tiles_update", "tiles_flagged",
+                                                "tiles_remedy", "sweeps")},
+            "roofline": roofline_block("k_persistent (Steps 2-3)", LOOP_BYTES_PER_NODE, inst.n_nodes, loop_ms,
+                                       captured_traffic(name))}
 
 
 def bench_paper_examples(args, dev, wsp, flush_buf):
@@ -467,30 +530,48 @@ def bench_paper_examples(args, dev, wsp, flush_buf):
 
 
 def bench_batched(args, dev, wsp, flush_buf):
-    """64 lognormal instances (edges 64..192): one batched solve vs one solve per instance."""
+    """64 lognormal instances (edges 64..192): one batched solve on the options the autotuner
+    picks for this problem class (tile shape x list order x one-launch schedule), replayed
+    from a CUDA graph, vs one default solve per instance."""
     import torch
-    from paper_2106_15869_b300 import api, workloads as W
+    from paper_2106_15869_b300 import api, autotune, workloads as W
     insts = W.lognormal_batch(64)
     n = sum(i.n_nodes for i in insts)
     probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h) for i in insts]
-    bs = api.BatchedSolver(probs, graph=True)       # one persistent launch, replayed from a CUDA graph
+    t0 = time.perf_counter()
+    tuned = autotune.tune(probs, reps=2)
+    tune_s = time.perf_counter() - t0
+    opts = {k: v for k, v in tuned.items() if not k.startswith("_")}
+    bs = api.BatchedSolver(probs, graph=True, **opts)     # one cooperative launch, replayed from a CUDA graph
     batched = bs.solve
     plain = lambda: [api.solve(p[0], p[1], p[2], workspace=wsp) for p in probs]
     batched(); plain()
-    tb = _timed(batched, flush_buf, 3)
+    tb = _timed(batched, flush_buf, 5)
     tp = _timed(plain, flush_buf, 2)
-    st = bs.stats()
+    loops = []
+    for _ in range(3):
+        flush_buf.zero_()
+        st = bs.stats()
+        loops.append(st["ms_loop"])
+    loop_ms = statistics.median(loops)
+    default = all(v == d for v, d in ((opts.get("tile"), "8x8x8"), (opts.get("order"), 0.0),
+                                      (opts.get("schedule"), "persistent")))
     return {"workload": "lognormal_batch64 (64 instances, edges 64..192, F = exp(0.3 g))", "nodes": n,
-            "graph_replay": True,
+            "tuned_options": opts, "tuning_ms": tuned.get("_ms"), "tuning_s": tune_s, "graph_replay": True,
             "batched_ms": tb, "batched_nodes_per_s": n / (tb / 1e3), "plain_loop_ms": tp,
             "plain_loop_nodes_per_s": n / (tp / 1e3), "speedup_vs_plain": tp / tb,
-            "loop_ms": st["ms_loop"], "loop_gbs_algorithmic": LOOP_BYTES_PER_NODE * n / (st["ms_loop"] / 1e3) / 1e9}
+            "solver_stats": {k: st[k] for k in ("iters_update", "iters_remedy", "tiles_update", "tiles_flagged",
+                                                "tiles_remedy", "sweeps")},
+            "roofline": roofline_block(f"k_persistent (Steps 2-3, batch of 64, {opts})", LOOP_BYTES_PER_NODE, n,
+                                       loop_ms, captured_traffic("lognormal_batch64") if default else None,
+                                       loop_share_of_step=loop_ms / tb)}
 
 
 def bench_adjoint(args, dev, wsp, flush_buf):
-    """Tomography 192^3, 16 shots, 256 receivers: forward (one batched solve of the 16 shots on one
-    slowness model) + adjoint (one batched adjoint, gradients summed) vs the forward alone and vs 16
-    plain single solves."""
+    """Tomography 192^3, 16 shots, 256 receivers, at the configured initial slowness s = 1:
+    forward (one batched solve of the 16 shots on one slowness model) + adjoint (one batched
+    adjoint, gradients summed) vs the forward alone and vs 16 plain single solves; the loop
+    kernels' rooflines."""
     import torch
     from paper_2106_15869_b300 import api, workloads as W
     t = W.tomography_3d(192)
@@ -514,14 +595,80 @@ def bench_adjoint(args, dev, wsp, flush_buf):
     tb = _timed(both, flush_buf, 3)
     tp = _timed(plain, flush_buf, 2)
     n = F.numel() * len(shots)
-    _, ast = api.adjoint_batched(probs, phis, rs, shared_F=True, sum_instances=True, workspace=wsp,
-                                 return_stats=True)
-    return {"workload": "tomography 192^3, 16 shots, 256 receivers", "nodes_per_pass": n,
+    f_loop, a_loop = [], []
+    for _ in range(3):
+        flush_buf.zero_()
+        _, fst = api.solve_batched(probs, shared_F=True, workspace=wsp, return_stats=True)
+        flush_buf.zero_()
+        _, ast = api.adjoint_batched(probs, phis, rs, shared_F=True, sum_instances=True, workspace=wsp,
+                                     return_stats=True)
+        f_loop.append(fst["ms_loop"])
+        a_loop.append(ast["ms_loop"])
+    fl, al = statistics.median(f_loop), statistics.median(a_loop)
+    return {"workload": "tomography 192^3, 16 shots, 256 receivers, s = 1", "nodes_per_pass": n,
             "adjoint_stats": {"iterations": ast["iters_remedy"], "tile_visits": ast["tiles_remedy"],
-                              "sweeps": ast["sweeps"], "loop_ms": ast["ms_loop"]},
+                              "sweeps": ast["sweeps"], "loop_ms": al},
             "forward_ms": tf, "adjoint_ms": ta, "forward_plus_adjoint_ms": tb,
             "fwd_adj_over_fwd": tb / tf, "plain_16_solves_ms": tp, "forward_speedup_vs_plain": tp / tf,
-            "forward_nodes_per_s": n / (tf / 1e3), "fwd_adj_nodes_per_s": n / (tb / 1e3)}
+            "forward_nodes_per_s": n / (tf / 1e3), "fwd_adj_nodes_per_s": n / (tb / 1e3),
+            "roofline": {
+                "forward": roofline_block("k_persistent (16 shots, shared speeds)", LOOP_BYTES_PER_NODE, n, fl,
+                                          captured_traffic("tomography_192_forward")),
+                "adjoint": roofline_block("k_adj_persistent (16 shots, gradients summed)", ADJ_LOOP_BYTES_PER_NODE,
+                                          n, al, captured_traffic("tomography_192_adjoint", ADJOINT_SOURCES)),
+                "forward_plus_adjoint": roofline_block("both loop kernels", LOOP_BYTES_PER_NODE
+                                                       + ADJ_LOOP_BYTES_PER_NODE, n, fl + al)}}
+
+
+def cpu_baseline_batch(k: int) -> dict:
+    """The oracle's fast marching on the first k instances of the 64-instance batch, one
+    instance per host core (a thread pool; ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import numpy as np
+    import oracle
+    from paper_2106_15869_b300 import workloads as W
+    insts = W.lognormal_batch(64)[:k]
+    cores = min(host_cores(), k)
+    run = lambda i: oracle.fmm(i.F.astype(np.float32).astype(np.float64), i.h, i.src_idx, i.src_val)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(run, insts))
+    dt = time.perf_counter() - t0
+    nodes = sum(i.n_nodes for i in insts)
+    return {"value": nodes / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": f"first {k} of the 64 lognormal instances ({nodes} nodes), FMM per instance, "
+                      f"one instance per thread"}
+
+
+def cpu_baseline_tomography(k: int) -> dict:
+    """The oracle's forward (fast marching) and adjoint (back substitution) for k of the 16
+    shots of the 192^3 tomography at s = 1, one shot per host core."""
+    from concurrent.futures import ThreadPoolExecutor
+    import numpy as np
+    import oracle
+    from paper_2106_15869_b300 import workloads as W
+    t = W.tomography_3d(192)
+    F = 1.0 / np.asarray(t["s_init"], dtype=np.float64)
+    rec = t["receivers"]
+    shots = [int(s) for s in t["sources"][:k]]
+    cores = min(host_cores(), k)
+
+    def one(s):
+        phi = oracle.fmm(F, t["h"], [s])
+        r = np.zeros(phi.size)
+        r[rec] = 1.0
+        t1 = time.perf_counter()
+        oracle.adjoint(F, t["h"], [s], phi, r.reshape(phi.shape))
+        return time.perf_counter() - t1
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        adj_s = list(ex.map(one, shots))
+    dt = time.perf_counter() - t0
+    nodes = F.size * k
+    return {"value": nodes / dt, "unit": "nodes/s (forward + adjoint)", "cores": cores, "kind": "oracle",
+            "seconds": dt, "adjoint_share": sum(adj_s) / (dt * cores),
+            "sample": f"{k} of the 16 shots, FMM forward + reverse-order adjoint per shot, one shot per thread"}
 
 
 def main():
@@ -530,8 +677,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="oscillating_256",
-                    choices=["oscillating_256", "point_source_128", "maze_512", "lognormal_batch64"])
+    ap.add_argument("--workload", default="maze_512",
+                    choices=["maze_512", "oscillating_256", "point_source_128", "lognormal_batch64"])
     ap.add_argument("--tile", default="auto")
     ap.add_argument("--schedule", default="auto")
     ap.add_argument("--converge", default="auto", choices=["auto", "confirm", "sweep"])
@@ -541,7 +688,7 @@ def main():
                     help="list order: 0 default bucketed, >0 bucket width, <0 unordered")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FIM comparison, batched, adjoint and paper-example measurements")
+                    help="skip the secondary workloads, FIM comparison, batched, adjoint and paper examples")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -52,7 +52,8 @@ extern "C" {
 #define EIK_ERR_ARG 1          /* invalid argument (dims, h, pointer, workspace, source index) */
 #define EIK_ERR_NOCONVERGE 2   /* iteration cap reached; phi holds valid upper bounds */
 #define EIK_ERR_CUDA 3         /* a CUDA launch or runtime call failed */
-#define EIK_ERR_DEVICE 4       /* a bounded device-side wait timed out; phi holds upper bounds */
+#define EIK_ERR_DEVICE 4       /* a bounded device-side wait timed out (eik_options.wait_limit_us);
+                                  phi holds upper bounds */
 
 /* tile shapes (nodes per tile along x, y, z) */
 #define EIK_TILE_AUTO 0
@@ -114,12 +115,18 @@ typedef struct {
     int64_t max_iters;    /* cap per loop (update, remedy); 0 = automatic */
     int32_t precision;    /* EIK_FP32 / EIK_FP64 */
     int32_t skip_remedy;  /* 1 = stop after Step 2 (ablation; the result may be wrong) */
-    float order;          /* list order: 0 = default (bucketed, width 4), > 0 = bucket width in
-                             tile-crossing times, < 0 = unordered (every listed tile visited in
-                             every iteration, the schedule of Algorithm 2 as printed) */
+    float order;          /* list order: 0 = default (the Step-3 and FIM lists bucketed with width
+                             4, the Step-2 lists unordered), > 0 = both loops bucketed with this
+                             width in tile-crossing times (the mean crossing time, from the mean
+                             slowness), < 0 = unordered (every listed tile visited in every
+                             iteration, the schedule of Algorithm 2 as printed) */
     int32_t converge;     /* Step-2 convergence test of a tile (EIK_CONVERGE_*) */
     int32_t method;       /* EIK_METHOD_* (0 = IFIM) */
-    int32_t reserved;     /* must be 0 */
+    int32_t wait_limit_us; /* bound on every device-side wait of the call (grid barriers, queue
+                              slots), microseconds of %globaltimer; 0 = 2 s.  A wait that runs out
+                              raises device flag bit 1, every thread block leaves the launch, phi
+                              keeps valid upper bounds and the call reports EIK_ERR_DEVICE.  < 0 is
+                              EIK_ERR_ARG. */
 } eik_options;
 
 /* run statistics (filled when a stats pointer is passed; the call then synchronises) */
@@ -247,9 +254,12 @@ int eik_backtrace(const eik_grid *grid, int precision, const void *phi, const in
  * framework that owns all device memory and cannot lend a workspace.
  * Scratch comes from one static device array of 64 MiB built into the
  * library (held by every GPU that loads it, until the process exits); grids
- * whose eik_workspace_size() exceeds it are rejected with EIK_ERR_ARG.  The
- * first call on a device resolves the array's device address (a one-time
- * set-up per device): make that first call before any stream capture.  All
+ * whose eik_workspace_size() exceeds it are rejected with EIK_ERR_ARG.  Every
+ * call made outside stream capture looks up the array's device address on the
+ * current device (so a cudaDeviceReset() in between is harmless); a call made
+ * while `stream` is being captured reuses the address of the last uncaptured
+ * call on that device, so make one call on each device before any capture
+ * (EIK_ERR_ARG otherwise).  All
  * calls share the one array: calls whose work overlaps on a GPU race and
  * corrupt each other's results, so serialise them (one stream, or events).
  * Arguments, results and errors as for eik_solve.
@@ -261,8 +271,10 @@ int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_id
  * Diagnostics: per-iteration trace of the persistent schedule on the current
  * device.  While a buffer is set, every solve on that device writes into it:
  * buf[0] = number of records, then records of 4 uint64 = {globaltimer ns,
- * phase (0 start, 1 Step-2 iteration, 2 Step-3 seed pass, 3 remedy iteration),
- * list size, tiles visited}, one after each iteration's barrier, up to
+ * phase (0 start, 1 Step-2 iteration, 2 Step-3 seed pass, 3 remedy iteration,
+ * 4 iteration of the FIM loop; plus 256 when the iteration ran in throughput
+ * mode, a warp per tile, instead of a thread group per tile), list size,
+ * tiles visited}, one after each iteration's barrier, up to
  * `capacity` records (the buffer needs 4*capacity + 1 uint64, device memory,
  * 8-byte aligned).  Pass NULL to stop tracing.  Not synchronised with running
  * solves: set it between them.

@@ -10,6 +10,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libeikonal.so")
+# the same library with device-side index and NaN checks (compiled with -DEIK_DEBUG)
+LIB_DEBUG_PATH = os.path.join(HERE, "libeikonal_debug.so")
 
 EIK_OK = 0
 EIK_ERR_ARG = 1
@@ -33,7 +35,7 @@ class eik_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("skip_remedy", ctypes.c_int32), ("order", ctypes.c_float),
-                ("converge", ctypes.c_int32), ("method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("converge", ctypes.c_int32), ("method", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
 class eik_stats(ctypes.Structure):
@@ -55,6 +57,7 @@ class EikonalError(RuntimeError):
 
 
 _lib = None
+_lib_debug = None
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
 _i64 = ctypes.c_int64
@@ -64,12 +67,26 @@ _pi64 = ctypes.POINTER(ctypes.c_int64)
 def load():
     """Load libeikonal.so (built in-tree by paper_2106_15869_b300.build)."""
     global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libeikonal.so is not built ({LIB_PATH}); run "
+    if _lib is None:
+        _lib = _open(LIB_PATH)
+    return _lib
+
+
+def load_debug():
+    """Load libeikonal_debug.so: the same entry points, with the device-side checks of the
+    debug build (a tile id out of range or a NaN in phi/lambda raises a device flag and
+    the call returns EIK_ERR_DEVICE; nothing traps).  For tests and diagnosis."""
+    global _lib_debug
+    if _lib_debug is None:
+        _lib_debug = _open(LIB_DEBUG_PATH)
+    return _lib_debug
+
+
+def _open(path):
+    if not os.path.exists(path):
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run "
                           "`python -m paper_2106_15869_b300.build` (needs nvcc)")
-    lib = ctypes.CDLL(LIB_PATH)
+    lib = ctypes.CDLL(path)
     G = ctypes.POINTER(eik_grid)
     O = ctypes.POINTER(eik_options)
     S = ctypes.POINTER(eik_stats)
@@ -87,7 +104,6 @@ def load():
     lib.eik_version.restype = ctypes.c_char_p
     lib.eik_version.argtypes = []
     _optional_symbols(lib)
-    _lib = lib
     return lib
 
 
@@ -117,14 +133,14 @@ def _optional_symbols(lib):
         lib.eik_backtrace.argtypes = [G, ctypes.c_int, _vp, _vp, _i64, _i64, _vp, _vp, _vp]
 
 
-def check(rc: int):
+def check(rc: int, lib=None):
     if rc != EIK_OK:
-        msg = load().eik_last_error().decode(errors="replace")
+        msg = (lib or load()).eik_last_error().decode(errors="replace")
         raise EikonalError(rc, msg)
 
 
 def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=False,
-                 max_iters=0, order=0.0, converge="auto", method="ifim") -> eik_options:
+                 max_iters=0, order=0.0, converge="auto", method="ifim", wait_limit_us=0) -> eik_options:
     o = eik_options()
     o.tile = TILES[tile] if isinstance(tile, str) else int(tile)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -134,6 +150,7 @@ def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=Fal
     o.order = float(order)
     o.converge = CONVERGE[converge] if isinstance(converge, str) else int(converge)
     o.method = METHODS[method] if isinstance(method, str) else int(method)
+    o.wait_limit_us = int(wait_limit_us)
     return o
 
 

@@ -76,7 +76,7 @@ def _workspace(device, nbytes, ws: Workspace | None):
 
 def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", schedule="auto",
           skip_remedy=False, max_iters=0, order=0.0, converge="auto", method="ifim", return_stats=False,
-          workspace: Workspace | None = None, out: torch.Tensor | None = None):
+          workspace: Workspace | None = None, out: torch.Tensor | None = None, wait_limit_us: int = 0):
     """Arrival times phi of ||grad phi|| = 1/F with fixed values at the sources.
 
     F: (ny, nx) or (nz, ny, nx) float32 (or float64 = FP64 validation mode)
@@ -84,9 +84,12 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     (default 0); h: grid spacing, or (hx, hy[, hz]) for unequal spacings
     (eq. 5/6 with dx, dy, dz).  Returns phi with F's shape, dtype and device
     (+inf where unreachable); with return_stats also a dict of run statistics
-    (this synchronises the stream).  order: 0 = default bucketed list order,
-    > 0 = bucket width in tile-crossing times, < 0 = unordered lists (every
+    (this synchronises the stream).  order: 0 = default (the Step-3 lists
+    bucketed, the Step-2 lists unordered), > 0 = both loops bucketed with this
+    width in tile-crossing times, < 0 = unordered lists (every
     listed tile visited in every iteration, as Algorithm 2 is printed).
+    wait_limit_us: bound on every device-side wait (0 = 2 s); a wait that runs
+    out ends the launch with EIK_ERR_DEVICE and phi holding upper bounds.
     method: "ifim" (Algorithm 2: Step 2 without neighbour checks, then the
     remedy) or "fim" (the fast iterative method of Sec. 2.3 at tile
     granularity: neighbour tiles are re-listed when a visit lowers their
@@ -102,7 +105,8 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     val = _as_values(src_val, idx.numel(), Fd.dtype, dev)
     lib = _lib.load()
     g = _lib.grids_array([(nx, ny, nz, h)])
-    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge, method)
+    opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge, method,
+                            wait_limit_us)
     nbytes = lib.eik_workspace_size(g, ctypes.byref(opt))
     if nbytes == 0:
         raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grid or options")
@@ -122,7 +126,7 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
 
 def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, max_iters=0, order=0.0,
                   converge="auto", method="ifim", return_stats=False, workspace: Workspace | None = None,
-                  shared_F: bool = False):
+                  shared_F: bool = False, wait_limit_us: int = 0):
     """Solve many independent grids in one set of launches.
 
     problems: list of (F, src_idx, h) or (F, src_idx, h, src_val); all F on the
@@ -164,7 +168,8 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
     src_val = torch.cat(vals) if sum(nsrc) else torch.zeros(0, dtype=dtype, device=dev)
     lib = _lib.load()
     g = _lib.grids_array(dims)
-    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge, method)
+    opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge, method,
+                            wait_limit_us)
     B = len(problems)
     nbytes = lib.eik_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:
@@ -187,7 +192,8 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
 
 
 def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances: bool = False, tile="auto",
-                    max_iters=0, order=0.0, return_stats=False, workspace: Workspace | None = None):
+                    max_iters=0, order=0.0, return_stats=False, workspace: Workspace | None = None,
+                    wait_limit_us: int = 0):
     """Gradients dL/ds (s = 1/F) of a loss L(phi) by the adjoint of the discrete solve.
 
     problems: list of (F, src_idx, h) as for solve_batched (all on one CUDA
@@ -239,7 +245,7 @@ def adjoint_batched(problems, phis, rs, *, shared_F: bool = False, sum_instances
     src_idx = torch.cat(idxs) if sum(nsrc) else torch.zeros(0, dtype=torch.int64, device=dev)
     lib = _lib.load()
     g = _lib.grids_array(dims)
-    opt = _lib.make_options(tile, "auto", _DT[dtype], False, max_iters, order)
+    opt = _lib.make_options(tile, "auto", _DT[dtype], False, max_iters, order, wait_limit_us=wait_limit_us)
     B = len(problems)
     nbytes = lib.eik_adjoint_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:
@@ -328,7 +334,7 @@ class Trace:
 
         with api.Trace() as tr:
             api.solve(...)
-        tr.records   # numpy (n, 4): time ns, phase, list size, tiles visited
+        tr.records   # numpy (n, 4): time ns, phase (+256: throughput mode), list size, tiles visited
     """
 
     def __init__(self, capacity: int = 1 << 16, device=None):
@@ -359,14 +365,15 @@ class Trace:
         if r is None or len(r) < 2:
             return {}
         dt = np.diff(r[:, 0]) / 1e3
-        ph = r[1:, 1]
+        ph = r[1:, 1] & 0xff
+        thr = (r[1:, 1] & 256) != 0
         out = {}
         for p, name in ((1, "update"), (2, "seed"), (3, "remedy"), (4, "fim")):
             m = ph == p
             if m.any():
                 out[name] = dict(iterations=int(m.sum()), total_us=float(dt[m].sum()),
                                  median_us=float(np.median(dt[m])), mean_list=float(r[1:, 2][m].mean()),
-                                 visited=int(r[1:, 3][m].sum()))
+                                 visited=int(r[1:, 3][m].sum()), throughput_iterations=int((m & thr).sum()))
         return out
 
 
@@ -386,7 +393,7 @@ class BatchedSolver:
     """
 
     def __init__(self, problems, *, tile="auto", order=0.0, converge="auto", method="ifim", max_iters=0,
-                 graph=True):
+                 graph=True, schedule="persistent"):
         F0 = problems[0][0]
         self.device, self.dtype = F0.device, F0.dtype
         if self.dtype not in _DT or not F0.is_cuda:
@@ -410,8 +417,11 @@ class BatchedSolver:
         self.src_val = torch.cat(vals) if sum(self.nsrc) else torch.zeros(1, dtype=self.dtype, device=self.device)
         self._lib = _lib.load()
         self._grids = _lib.grids_array(dims)
-        # the graph replays a fixed launch sequence: persistent schedule, no host reads
-        self._opt = _lib.make_options(tile, "persistent", _DT[self.dtype], False, max_iters, order, converge, method)
+        # the graph replays a fixed launch sequence: one cooperative launch (the persistent
+        # kernel or the asynchronous work queue), no host reads
+        if schedule not in ("persistent", "async"):
+            raise ValueError("a captured batch runs the persistent or the asynchronous schedule")
+        self._opt = _lib.make_options(tile, schedule, _DT[self.dtype], False, max_iters, order, converge, method)
         self._Foff, self._poff, self._soff = (_lib.i64_array(self.off), _lib.i64_array(self.off),
                                               _lib.i64_array(self.src_off))
         nbytes = self._lib.eik_workspace_size_batched(len(problems), self._grids, ctypes.byref(self._opt))

@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libeikonal.so")
+# the same sources with the device-side checks of the debug build (-DEIK_DEBUG)
+LIB_DEBUG = os.path.join(HERE, "libeikonal_debug.so")
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
@@ -38,26 +40,38 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile csrc/eik_api.cu into libeikonal.so next to this file."""
-    if not force and not needs_build():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, *(extra_flags or []), "-o", tmp, os.path.join(CSRC, "eik_api.cu")]
+def _compile(lib: str, flags: list[str], verbose: bool) -> subprocess.Popen:
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *NVCC_FLAGS, *flags, "-o", tmp, os.path.join(CSRC, "eik_api.cu")]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    return subprocess.Popen(cmd), tmp
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = True) -> str:
+    """Compile csrc/eik_api.cu into libeikonal.so next to this file, and (debug=True) the
+    checked build libeikonal_debug.so beside it; the two nvcc runs go in parallel."""
+    jobs = []
+    if force or needs_build(LIB):
+        jobs.append((LIB, *_compile(LIB, list(extra_flags or []), verbose)))
+    if debug and (force or needs_build(LIB_DEBUG)):
+        jobs.append((LIB_DEBUG, *_compile(LIB_DEBUG, ["-DEIK_DEBUG", *(extra_flags or [])], verbose)))
+    for lib, proc, tmp in jobs:
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, "nvcc " + os.path.basename(lib))
+        os.replace(tmp, lib)
     return LIB
 
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)
     print(LIB)
+    print(LIB_DEBUG)

@@ -70,6 +70,7 @@ struct AdjParams {
     float *inst_scale;          // [B] 1/delta per instance
     int ordered;
     float order;
+    unsigned long long wait_ns;  // bound on every device wait of the call
 };
 
 template <int BX, int BY, int BZ>
@@ -353,7 +354,10 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
     }
 #pragma unroll
     for (int m = 0; m < NPT; ++m)
-        if (mine >> m & 1) __stcg(P.lam_t + (size_t)g * G::V + GG::node(gt, m), lam[m]);
+        if (mine >> m & 1) {
+            dbg_nan(P.ctl, lam[m]);
+            __stcg(P.lam_t + (size_t)g * G::V + GG::node(gt, m), lam[m]);
+        }
     return s;
 }
 
@@ -447,8 +451,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
             int *vcnt = &ctl->rvcnt[r % 3];
             for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
                 const int e = e0 + lane;
-                const bool valid = e < n;
+                bool valid = e < n;
                 const int g = valid ? __ldcg(in + e) : -1;
+                if (valid && dbg_bad_tile(ctl, g, P.n_tiles)) valid = false;
                 int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
                 if (valid) {
                     r0 = __ldcg(reinterpret_cast<const int4 *>(P.tile_rec + 8 * g));
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
                 warp_push(ctl, &ctl->rcnt[nslot], out, P.n_tiles, want, g, ord.on ? &ctl->rkmin[nslot] : nullptr, key);
                 push_visit(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g, key, r0, r1);
             }
-            if (!grid_sync(ctl, target)) break;
+            if (!grid_sync(ctl, target, P.wait_ns)) break;
             const int nv = min(ld_volatile(vcnt), P.n_tiles);
             __shared__ int s_tile[GG::NG];
             for (bool first = true;; first = false) {
@@ -474,6 +479,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
                     if (idx < nv) {
                         const VisitRec *vr = P.vlist + idx;
                         g = __ldcg(&vr->head).x;
+                        if (dbg_bad_tile(ctl, g, P.n_tiles)) g = -1;
                         const int4 a = __ldcg(&vr->r0), b = __ldcg(&vr->r1);
                         s_nb[gi][0] = a.x; s_nb[gi][1] = a.y; s_nb[gi][2] = a.z; s_nb[gi][3] = a.w;
                         s_nb[gi][4] = b.x; s_nb[gi][5] = b.y;
@@ -505,8 +511,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
                 if (base >= n) break;                          // group-uniform
                 {
                     const int e = base + gt;
-                    const bool valid = gt < chunk && e < n;
+                    bool valid = gt < chunk && e < n;
                     const int g = valid ? __ldcg(in + e) : -1;
+                    if (valid && dbg_bad_tile(ctl, g, P.n_tiles)) valid = false;
                     const unsigned key = valid && ord.on ? __ldg(P.tkey + g) : kKeyInf;
                     const bool defer = valid && ord.on && !order_visit(ord, key);
                     bool want = false;
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
         }
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
-        if (!grid_sync(ctl, target)) break;
+        if (!grid_sync(ctl, target, P.wait_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters_remedy = r;
     // visits and sweeps are counted by thread 0 of each group, deferrals by the classifying threads

@@ -66,7 +66,9 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Opts {
     int tile, schedule, precision, skip_remedy, converge, method;
     long long max_iters;
+    unsigned long long wait_ns;   // bound on every device wait (kWaitLimitNs unless the call sets one)
     float order;           // <= 0: unordered lists (every listed tile visited each iteration)
+    bool order_update;     // the Step-2 lists are bucketed too (an explicit order > 0)
 };
 
 constexpr float kDefaultOrder = 4.0f;          // bucket width (tile-crossing times) of the default schedule
@@ -80,7 +82,11 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
     out.max_iters = o ? o->max_iters : 0;
     const float ord = o ? o->order : 0.0f;
     if (!(ord == ord)) return false;                       // NaN
+    // default: the Step-3 (and FIM) lists bucketed with width kDefaultOrder, the Step-2
+    // lists unordered (every Active tile visited in every iteration, as Algorithm 2 is
+    // printed); an explicit order > 0 buckets both loops with that width
     out.order = ord == 0.0f ? kDefaultOrder : (ord < 0.0f ? 0.0f : ord);
+    out.order_update = ord > 0.0f;
     out.converge = o ? o->converge : EIK_CONVERGE_AUTO;
     if (out.converge < 0 || out.converge > EIK_CONVERGE_SWEEP) return false;
     if (out.converge == EIK_CONVERGE_AUTO) out.converge = EIK_CONVERGE_CONFIRM;
@@ -90,7 +96,9 @@ bool read_opts(const eik_options *o, int64_t B, const eik_grid *grids, Opts &out
         out.converge = EIK_CONVERGE_SWEEP;                  // a visit relaxes to the tile's local fixed point
         out.skip_remedy = 0;
     }
-    if (o && o->reserved != 0) return false;
+    const long long wl = o ? (long long)o->wait_limit_us : 0;
+    if (wl < 0) return false;
+    out.wait_ns = wl > 0 ? (unsigned long long)wl * 1000ull : kWaitLimitNs;
     if (out.precision != EIK_FP32 && out.precision != EIK_FP64) return false;
     if (out.schedule < 0 || out.schedule > EIK_SCHED_ASYNC) return false;
     if (out.tile < 0 || out.tile > EIK_TILE_8x8x1) return false;
@@ -275,6 +283,8 @@ int finish_stats(Ctl *dctl, cudaStream_t st, eik_stats *stats, PhaseEvents *pe) 
     stats->device_flags = h.flags;
     int code = EIK_OK;
     if (h.flags & kFlagTimeout) code = fail(EIK_ERR_DEVICE, "a device-side wait timed out");
+    else if (h.flags & kFlagDebugIndex) code = fail(EIK_ERR_DEVICE, "debug check: a tile id out of range");
+    else if (h.flags & kFlagDebugNaN) code = fail(EIK_ERR_DEVICE, "debug check: NaN written to phi or lambda");
     else if (h.flags & kFlagOverflow) code = fail(EIK_ERR_DEVICE, "internal list overflow");
     else if (h.flags & kFlagBadSource) code = fail(EIK_ERR_ARG, "a source index lies outside its grid");
     else if (h.flags & kFlagCap) code = fail(EIK_ERR_NOCONVERGE, "iteration cap reached");
@@ -299,6 +309,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.scale_done = reinterpret_cast<int *>(ws + L.scale_done);
     P.tile_fstat = reinterpret_cast<float *>(ws + L.tile_fstat);
     P.ordered = o.order > 0.0f ? 1 : 0;
+    P.ordered_update = o.order_update ? 1 : 0;
     P.order = o.order;
     P.list0 = reinterpret_cast<int *>(ws + L.list0);
     P.list1 = reinterpret_cast<int *>(ws + L.list1);
@@ -323,6 +334,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     P.src_val = static_cast<const T *>(src_val);
     P.n_src = n_src;
     P.phi_out = static_cast<T *>(phi);
+    P.wait_ns = o.wait_ns;
     static_assert(sizeof(Ctl) / sizeof(int) <= kSpanThreads, "control block zeroing by the threads of one CTA");
 
     PhaseEvents pe;
@@ -377,6 +389,8 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
         Q.qstate = reinterpret_cast<int *>(ws + L.q_state);
         Q.mask = L.q_slots - 1;
         Q.visit_cap = P.max_iters * (long long)L.n_tiles;
+        Q.wait_ns = o.wait_ns;
+        Q.n_tiles = (int)L.n_tiles;
         int per_sm_a = 0;
         EIK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_async<T, BX, BY, BZ>, CTA, 0),
                  "occupancy query");
@@ -632,6 +646,7 @@ int run_adjoint(const AdjLayout &L, const Opts &o, char *ws, const void *F, cons
     P.inst_scale = reinterpret_cast<float *>(ws + L.inst_scale);
     P.ordered = o.order > 0.0f ? 1 : 0;
     P.order = o.order;
+    P.wait_ns = o.wait_ns;
     PhaseEvents pe;
     int rc = EIK_OK;
     if (stats && (rc = pe.create())) return rc;
@@ -748,17 +763,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device, resolved once
-// per device (the host-side name of the array is not a device address).
-int noalloc_scratch(void **out) {
+// Device address of g_noalloc_scratch on the current device (the host-side
+// name of the array is not a device address).  It is looked up again on every
+// call made outside stream capture -- a cheap host-side query once the module
+// is loaded, which also picks up a new address after cudaDeviceReset() -- and
+// remembered per device for calls made while `stream` is being captured, which
+// need an earlier uncaptured call on that device.
+int noalloc_scratch(cudaStream_t stream, void **out) {
     int dev = -1;
     EIK_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(EIK_ERR_ARG, "device index %d out of range", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    EIK_CUDA(cudaStreamIsCapturing(stream, &cap), "cudaStreamIsCapturing");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         EIK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
         g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+        return fail(EIK_ERR_ARG, "eik_solve_noalloc: make one call on this device outside stream capture first");
     }
     *out = g_scratch_addr[dev];
     return EIK_OK;
@@ -812,7 +835,7 @@ int eik_solve_noalloc(const eik_grid *grid, const void *F, const int64_t *src_id
                     "call eik_solve with a caller-provided workspace instead",
                     need, kNoAllocScratchBytes);
     void *scratch = nullptr;
-    const int rc = noalloc_scratch(&scratch);
+    const int rc = noalloc_scratch(static_cast<cudaStream_t>(stream), &scratch);
     if (rc) return rc;
     // the solve initialises every part of the workspace it reads (control
     // block, per-tile state, keys, lists), so stale contents of the shared

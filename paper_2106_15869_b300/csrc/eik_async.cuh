@@ -15,7 +15,7 @@
 // waits until seq == p, writes, sets seq = p + 1; the consumer of p waits
 // until seq == p + 1, reads, sets seq = p + Q).  Q exceeds the number of tiles
 // plus warps, so a producer never waits for a consumer that has not claimed
-// its position.  Every wait is bounded by kWaitLimitNs.
+// its position.  Every wait is bounded by the call's wait limit (Q.wait_ns).
 #pragma once
 
 #include "eik_kernels.cuh"
@@ -30,6 +30,8 @@ struct AsyncQ {
     int *qstate;                  // [n_tiles] QState
     unsigned long long mask;      // Q - 1
     long long visit_cap;          // visits allowed per phase
+    unsigned long long wait_ns;   // bound on every wait of the queue
+    int n_tiles;                  // tile ids in the ring lie in [0, n_tiles)
 };
 
 __device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long *p) {
@@ -47,7 +49,7 @@ __device__ __forceinline__ bool q_enqueue(Ctl *ctl, const AsyncQ &Q, int g) {
     const unsigned long long t0 = globaltimer();
     while (ld_acq_u64(sq) != p) {
         if (ld_volatile(&ctl->abort)) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) {
+        if (globaltimer() - t0 > Q.wait_ns) {
             atomicOr(&ctl->flags, kFlagTimeout);
             atomicExch(&ctl->abort, 1);
             return false;
@@ -99,6 +101,13 @@ __device__ __forceinline__ int q_pop(Ctl *ctl, const AsyncQ &Q) {
             if (sv == p + 1) {
                 const int e = __ldcg(Q.data + (p & Q.mask));
                 st_release(sq, p + Q.mask + 1);
+                if (dbg_bad_tile(ctl, e, Q.n_tiles)) {
+                    // debug build: an entry that is not a tile id is consumed and dropped
+                    atomicSub(&ctl->q_pending, 1);
+                    p = atomicAdd(&ctl->q_head, 1ull);
+                    t0 = globaltimer();
+                    continue;
+                }
                 if (!ld_volatile(&ctl->q_stop)) { g = e; break; }
                 // draining after the visit cap: drop the entry, claim the next position
                 __stcg(Q.qstate + e, (int)kIdle);
@@ -114,7 +123,7 @@ __device__ __forceinline__ int q_pop(Ctl *ctl, const AsyncQ &Q) {
                 break;
             }
             if (ld_volatile(&ctl->abort)) break;
-            if (globaltimer() - t0 > kWaitLimitNs) {
+            if (globaltimer() - t0 > Q.wait_ns) {
                 atomicOr(&ctl->flags, kFlagTimeout);
                 atomicExch(&ctl->abort, 1);
                 break;
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
     long long t_upd = 0, t_flag = 0, t_rem = 0, sweeps = 0;
     if (P.fim) goto neighbour_check;                   // FIM: the queue holds the source tiles
     async_update_phase<T, BX, BY, BZ>(P, Q, my, t_upd, sweeps);
-    if (!grid_sync(ctl, target)) goto done;
+    if (!grid_sync(ctl, target, P.wait_ns)) goto done;
     if (ld_volatile(&ctl->q_stop) || P.skip_remedy) goto done;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // every claimed position was consumed or retired: restart the ring there
@@ -261,9 +270,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
         ctl->q_pending = 0;
         ctl->q_visits = 0;
     }
-    if (!grid_sync(ctl, target)) goto done;
+    if (!grid_sync(ctl, target, P.wait_ns)) goto done;
     async_detect_pass<T, BX, BY, BZ>(P, Q, my, t_flag);
-    if (!grid_sync(ctl, target)) goto done;
+    if (!grid_sync(ctl, target, P.wait_ns)) goto done;
 neighbour_check:
     async_remedy_phase<T, BX, BY, BZ>(P, Q, my, t_rem, sweeps);
 done:

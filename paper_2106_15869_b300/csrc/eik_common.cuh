@@ -22,13 +22,28 @@
 namespace eik {
 
 constexpr int kMaxInstPerLaunch = 128;       // descriptors passed by value per launch
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s bound on every device wait
+// default bound on every device wait (2 s); a call may set another (eik_options.wait_limit_us)
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // device flag bits (eik_stats.device_flags)
 constexpr int kFlagCap = 1;          // iteration cap reached
 constexpr int kFlagTimeout = 2;      // a bounded wait gave up
 constexpr int kFlagBadSource = 4;    // a source index outside its grid (ignored)
 constexpr int kFlagOverflow = 8;     // a list push beyond capacity (internal error)
+constexpr int kFlagDebugIndex = 16;  // EIK_DEBUG builds: a tile id read from a list or queue out of range
+constexpr int kFlagDebugNaN = 32;    // EIK_DEBUG builds: a NaN written to phi or lambda
+
+// Debug build (compiled with -DEIK_DEBUG, libeikonal_debug.so): every tile id
+// read from a list, a visit record or the work queue is checked against the
+// tile count before use, and every value written back to phi or lambda is
+// checked for NaN.  A failed check raises a device flag (reported by the call
+// as EIK_ERR_DEVICE) and the access is skipped; nothing traps.  In the release
+// build the checks compile to nothing.
+#ifdef EIK_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
 
 enum TileState : int { kDistant = 0, kActive = 1, kSource = 2 };
 
@@ -78,6 +93,24 @@ struct Ctl {
     int rvcnt[3], rvgrab[3];             // the same for Step 3
 };
 static_assert(sizeof(Ctl) <= 256, "the control block is zeroed by 64 threads");
+
+// debug build: true (and the flag raised) when tile id g is outside [0, n)
+__device__ __forceinline__ bool dbg_bad_tile(Ctl *ctl, long long g, long long n) {
+    if constexpr (kDebug) {
+        if (g < 0 || g >= n) {
+            atomicOr(&ctl->flags, kFlagDebugIndex);
+            return true;
+        }
+    }
+    return false;
+}
+// debug build: raise the flag when a value written back is NaN
+template <class T>
+__device__ __forceinline__ void dbg_nan(Ctl *ctl, T v) {
+    if constexpr (kDebug) {
+        if (v != v) atomicOr(&ctl->flags, kFlagDebugNaN);
+    }
+}
 
 // Ordered-float encoding for atomicMin on keys: monotone as unsigned.
 __device__ __forceinline__ unsigned key_enc(float k) {
@@ -276,9 +309,9 @@ __device__ __forceinline__ T node_solve(T ax, T ay, T az, T tau, const Metric<T>
 }
 
 // Device-wide barrier for a cooperative launch.  Every wait is bounded by
-// kWaitLimitNs; on a timeout the block raises ctl->abort and every block
-// leaves at its next barrier.  Returns false when the launch must stop.
-__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned long long &target) {
+// limit_ns of %globaltimer; on a timeout the block raises ctl->abort and every
+// block leaves at its next barrier.  Returns false when the launch must stop.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned long long &target, unsigned long long limit_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -289,7 +322,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned long long &target) 
         int ok = 1;
         while (ld_acquire(&ctl->bar) < target) {
             if (ld_volatile(&ctl->abort)) { ok = 0; break; }
-            if (globaltimer() - t0 > kWaitLimitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 atomicOr(&ctl->flags, kFlagTimeout);
                 atomicExch(&ctl->abort, 1);
                 ok = 0;

@@ -53,8 +53,9 @@ struct FwdParams {
     float *inst_scale;           // [B] 1/delta of each instance (ordered schedule)
     ScalePart *scale_part;       // [B][scale_chunks(B)] partial speed statistics (k_scale)
     int *scale_done;             // [B] k_scale CTAs finished per instance
-    float *tile_fstat;           // [n_tiles][4] sum, count, min, max of the passable speeds (for delta)
-    int ordered;                 // 1 = bucketed order of the lists
+    float *tile_fstat;           // [n_tiles][4] sum of 1/F, count, min F, max F over passable nodes (delta)
+    int ordered;                 // 1 = bucketed order of the Step-3 (and FIM) lists; keys are kept
+    int ordered_update;          // 1 = bucketed order of the Step-2 lists too
     float order;                 // bucket width in tile-crossing times
     int *list0, *list1;
     VisitRec *vlist;             // the tiles kept by the classification of a two-phase iteration
@@ -71,6 +72,7 @@ struct FwdParams {
     const T *src_val;
     long long n_src;
     T *phi_out;                  // packed output
+    unsigned long long wait_ns;  // bound on every device wait of the call
 };
 
 template <int BX, int BY, int BZ>
@@ -245,7 +247,10 @@ __device__ __forceinline__ void write_back(const FwdParams<T> &P, int g, unsigne
     T *pg = P.phi_t + (size_t)g * G::V;
 #pragma unroll
     for (int m = 0; m < G::NPL; ++m)
-        if (mine >> m & 1) __stcg(pg + lane_id() + 32 * m, v[m]);
+        if (mine >> m & 1) {
+            dbg_nan(P.ctl, v[m]);
+            __stcg(pg + lane_id() + 32 * m, v[m]);
+        }
 }
 
 // Static assignment of list entries: warp w of the launch takes entries
@@ -313,10 +318,11 @@ __device__ void update_pass(const FwdParams<T> &P, T *sm, int it, int n, unsigne
     unsigned *kcur = P.tkey + (size_t)(it & 1) * P.n_tiles;
     unsigned *knext = P.tkey + (size_t)((it + 1) & 1) * P.n_tiles;
     const int lane = lane_id();
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    const OrderCtx ord = order_begin(P.ordered_update, kmin_cur, width);
     n = min(n, P.n_tiles);                       // n > n_tiles only after an overflow
     for (int idx = warp_global(); idx < n; idx += warps_total()) {
         const int g = __ldcg(in + idx);
+        if (dbg_bad_tile(ctl, g, P.n_tiles)) continue;             // warp-uniform
         // one round trip: the tile record (lanes 0-7) and its key (lane 8)
         const int rec = lane < 8 ? __ldcg(P.tile_nb + 8 * g + lane) : (lane == 8 && ord.on ? (int)__ldcg(kcur + g) : -1);
         const int nbf = lane < 6 ? rec : -1;
@@ -431,6 +437,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
     const int next_stamp = r + 2;
     for (int idx = warp_global(); idx < n; idx += warps_total()) {
         const int g = __ldcg(in + idx);
+        if (dbg_bad_tile(ctl, g, P.n_tiles)) continue;             // warp-uniform
         const int rec = lane < 8 ? __ldcg(P.tile_nb + 8 * g + lane) : (lane == 8 && ord.on ? (int)__ldcg(kcur + g) : -1);
         const int nbf = lane < 6 ? rec : -1;
         const float sc = __int_as_float(__shfl_sync(kFull, rec, 7));

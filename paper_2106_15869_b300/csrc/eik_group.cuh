@@ -143,7 +143,10 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     }
 #pragma unroll
     for (int m = 0; m < GG::NPT; ++m)
-        if (mine >> m & 1) __stcg(P.phi_t + (size_t)g * G::V + GG::node(gt, m), v[m]);
+        if (mine >> m & 1) {
+            dbg_nan(P.ctl, v[m]);
+            __stcg(P.phi_t + (size_t)g * G::V + GG::node(gt, m), v[m]);
+        }
     return s;
 }
 
@@ -303,7 +306,7 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
     T *sm = smbase + (size_t)gi * G::S;
     GroupCtl &gc = gcs[gi];
     GroupQueue &q = gqs[gi];
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    const OrderCtx ord = order_begin(remedy ? P.ordered : P.ordered_update, kmin_cur, width);
     n = min(n, P.n_tiles);
     chunk = max(1, min(chunk, GG::GT));
     const int cta_groups = blockDim.x / GG::GT;
@@ -322,8 +325,9 @@ __device__ void group_pass(const FwdParams<T> &P, T *smbase, GroupCtl *gcs, Grou
         // the tile record is loaded beside the key, for the first queued tiles
         {
             const int e = base + gt;
-            const bool valid = gt < chunk && e < n;
+            bool valid = gt < chunk && e < n;
             const int g = valid ? __ldcg(in + e) : -1;
+            if (valid && dbg_bad_tile(ctl, g, P.n_tiles)) valid = false;
             unsigned key = kKeyInf;
             int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
             if (valid) {
@@ -413,7 +417,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     int *vcnt = remedy ? &ctl->rvcnt[slot] : &ctl->vcnt[slot];
     int *vgrab = remedy ? &ctl->rvgrab[slot] : &ctl->vgrab[slot];
     const int next_stamp = it + 2;
-    const OrderCtx ord = order_begin(P.ordered, kmin_cur, width);
+    const OrderCtx ord = order_begin(remedy ? P.ordered : P.ordered_update, kmin_cur, width);
     n = min(n, P.n_tiles);
     // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the
     // pushes); a kept tile goes to the visit list with its key and record
@@ -421,8 +425,9 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     const int nthreads = gridDim.x * blockDim.x;
     for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
         const int e = e0 + lane;
-        const bool valid = e < n;
+        bool valid = e < n;
         const int g = valid ? __ldcg(in + e) : -1;
+        if (valid && dbg_bad_tile(ctl, g, P.n_tiles)) valid = false;
         unsigned key = kKeyInf;
         int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
         if (valid) {
@@ -443,7 +448,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
         warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
         push_visit(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g, key, r0, r1);
     }
-    if (!grid_sync(ctl, target)) return false;
+    if (!grid_sync(ctl, target, P.wait_ns)) return false;
     // visit the kept tiles
     const int tid = threadIdx.x;
     const int gi = tid / GG::GT, gt = tid % GG::GT, bid = 1 + gi;
@@ -459,6 +464,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
                 const VisitRec *vr = P.vlist + idx;
                 const int4 h = __ldcg(&vr->head);
                 group_set(gc, h.x, (unsigned)h.y, __ldcg(&vr->r0), __ldcg(&vr->r1));
+                if (dbg_bad_tile(ctl, h.x, P.n_tiles)) gc.tile = -1;
             } else {
                 gc.tile = -1;
             }

@@ -19,8 +19,10 @@ constexpr int kGroupModeFactor = 8;
 
 // Optional per-iteration trace of the persistent schedule (eik_set_trace):
 // records of 4 x u64 = {globaltimer ns, phase (1 Step 2, 2 Step-3 seed, 3
-// remedy, 4 FIM loop), list size, tiles visited}, written by thread 0 of CTA 0 after the
-// barrier that ends each iteration.
+// remedy, 4 FIM loop; plus kTraceThroughput when the iteration ran in
+// throughput mode, a warp per tile), list size, tiles visited}, written by
+// thread 0 of CTA 0 after the barrier that ends each iteration.
+constexpr unsigned long long kTraceThroughput = 256;
 __device__ unsigned long long *g_trace_buf = nullptr;
 __device__ long long g_trace_cap = 0;
 
@@ -47,10 +49,12 @@ __global__ void k_write_desc(InstDesc *desc, DescChunk chunk) {
 }
 
 // 1/delta per instance for the ordered schedule: delta = order * (mean tile
-// edge) * h / mean(F over passable nodes).  An instance whose passable speeds
-// span more than kOrderContrast (e.g. slow walls in a fast medium) spreads its
-// keys over too many buckets; it is left unordered (scale 0).
-constexpr double kOrderContrast = 100.0;
+// edge) * h * (mean slowness 1/F over passable nodes), `order` times the mean
+// time to cross a tile.  The mean slowness, not one over the mean speed: in a
+// medium of fast cells and slow walls (the maze: F = 1 and 1e-3) it follows
+// the walls, whose crossing times set the spread of the keys; with 1/mean(F)
+// the buckets were a few hundred times narrower there and an ordered solve of
+// the 512^3 maze took 4x the iterations.
 
 constexpr int kScaleThreads = 256;
 constexpr int kScaleUnroll = 8;      // independent loads in flight per thread
@@ -117,10 +121,11 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, c
         mn = fminf(mn, ld_volatile_f(&p.mn)); mx = fmaxf(mx, ld_volatile_f(&p.mx));
     }
     const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
-    const double meanF = cnt > 0 ? sum / cnt : 0.0;
-    double sc = meanF > 0 ? meanF / ((double)order * edge * d.h) : 1.0;
+    const double mean_slow = cnt > 0 ? sum / cnt : 0.0;
+    double sc = mean_slow > 0 ? 1.0 / ((double)order * edge * d.h * mean_slow) : 1.0;
     if (!(sc > 0) || !(sc < 1e30)) sc = 1.0;
-    if (cnt > 0 && (double)mx > kOrderContrast * (double)mn) sc = 0.0;
+    (void)mn;
+    (void)mx;
     inst_scale[b] = (float)sc;
 }
 
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
     constexpr int PER = kSpan * G::V / kSpanThreads;
     static_assert(kSpan * G::V % kSpanThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
     __shared__ TileSpan<BX, BY, BZ> sp;
-    __shared__ float s_acc[kSpan][4];          // sum, count, min, max of the passable speeds
+    __shared__ float s_acc[kSpan][4];          // sum of the slownesses 1/F, count, min and max F (passable nodes)
     const int tid = threadIdx.x;
     const long long total = (long long)P.n_tiles * G::V;
     for (long long g0 = (long long)blockIdx.x * kSpan; g0 < P.n_tiles; g0 += (long long)gridDim.x * kSpan) {
@@ -199,8 +204,9 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
                 P.phi_t[e] = Num<T>::inf();
             }
             if (P.ordered) {   // a warp's 32 nodes lie in one tile
-                float fs = pass ? (float)f[m] : 0.0f, fc = pass ? 1.0f : 0.0f;
-                float fmn = pass ? fs : __int_as_float(0x7f800000), fmx = fs;
+                const float fv = pass ? (float)f[m] : 0.0f;
+                float fs = pass ? 1.0f / fv : 0.0f, fc = pass ? 1.0f : 0.0f;
+                float fmn = pass ? fv : __int_as_float(0x7f800000), fmx = fv;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     fs += __shfl_xor_sync(0xffffffffu, fs, o);
@@ -423,6 +429,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
             ctl->vgrab[(it + 2) % 3] = 0;
             ctl->nproc[(it + 2) % 4] = 0;
         }
+        bool thr = false;                              // this iteration in throughput mode
         if constexpr (MODE == kPersistLatency) {
             // more visits expected (the last iteration's, or the list) than groups: smaller
             // groups, and the two-phase pass (classify the whole list, then one visit per grab)
@@ -437,21 +444,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
             update_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, it, n, kq, width, chunk, &s_visits, t_upd,
                                              sweeps, deferred);
         } else {
+            thr = true;
             update_pass<T, BX, BY, BZ>(P, my, it, n, kq, width, &s_visits, t_upd, sweeps, deferred);
         }
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[it % 4], s_visits); s_visits = 0; }
-        if (!grid_sync(ctl, target)) goto done;
-        trace_record(tk, 1, n, ld_volatile(&ctl->nproc[it % 4]));
+        if (!grid_sync(ctl, target, P.wait_ns)) goto done;
+        trace_record(tk, 1 | (thr ? kTraceThroughput : 0), n, ld_volatile(&ctl->nproc[it % 4]));
     }
     if (P.skip_remedy) goto done;
     detect_pass<T, BX, BY, BZ>(P, my, t_flag);
-    if (!grid_sync(ctl, target)) goto done;
+    if (!grid_sync(ctl, target, P.wait_ns)) goto done;
     trace_record(tk, 2, P.n_tiles, ld_volatile(&ctl->rcnt[0]));
     // the Step-2 counters are idle from here on: nproc slots restart for Step 3
     if (blockIdx.x == 0 && threadIdx.x == 0)
         for (int q = 0; q < 4; ++q) ctl->nproc[q] = 0;
-    if (!grid_sync(ctl, target)) goto done;
+    if (!grid_sync(ctl, target, P.wait_ns)) goto done;
 neighbour_check:
     // Step 3b; under the FIM the whole solve.  A visit lists the neighbour
     // tiles across the faces where its values dropped, whatever their state.
@@ -479,6 +487,7 @@ neighbour_check:
             ctl->rvgrab[(r + 2) % 3] = 0;
             ctl->nproc[(r + 2) % 4] = 0;
         }
+        bool thr = false;
         if constexpr (MODE == kPersistLatency) {
             if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (r > 0 ? s_p : n) > groups) {
                 if (!group_pass_split<T, BX, BY, BZ, true, kSmallGroupThreads>(
@@ -491,12 +500,13 @@ neighbour_check:
             remedy_pass_group<T, BX, BY, BZ>(P, &sm.phi[0][0], gcs, gqs, r, n, kq, width, chunk, &s_visits, t_rem,
                                              sweeps, deferred);
         } else {
+            thr = true;
             remedy_pass<T, BX, BY, BZ>(P, my, r, n, kq, width, &s_visits, t_rem, sweeps, deferred);
         }
         __syncthreads();
         if (threadIdx.x == 0 && s_visits) { atomicAdd(&ctl->nproc[r % 4], s_visits); s_visits = 0; }
-        if (!grid_sync(ctl, target)) goto done;
-        trace_record(tk, P.fim ? 4 : 3, n, ld_volatile(&ctl->nproc[r % 4]));
+        if (!grid_sync(ctl, target, P.wait_ns)) goto done;
+        trace_record(tk, (P.fim ? 4 : 3) | (thr ? kTraceThroughput : 0), n, ld_volatile(&ctl->nproc[r % 4]));
     }
 done:
     if (blockIdx.x == 0 && threadIdx.x == 0) {

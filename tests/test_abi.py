@@ -110,9 +110,8 @@ def test_host_argument_errors_before_device_work():
     assert lib.eik_solve(g, 1, None, None, -1, 1, 4096, 1 << 30, None, None, None) == _lib.EIK_ERR_ARG
     bad = _lib.grids_array([(8, 0, 8, 0.1)])
     assert lib.eik_solve(bad, 1, None, None, 0, 1, 4096, 1 << 30, None, None, None) == _lib.EIK_ERR_ARG
-    # the reserved option field must be zero; the method must be a known one
-    o2 = _lib.make_options()
-    o2.reserved = 3
+    # a negative wait limit is rejected; the method must be a known one
+    o2 = _lib.make_options(wait_limit_us=-1)
     assert lib.eik_solve(g, 1, None, None, 0, 1, 4096, 1 << 30, None, ctypes.byref(o2), None) == _lib.EIK_ERR_ARG
     for m in (-1, 2):
         o3 = _lib.make_options(method=m)

@@ -4,8 +4,10 @@ against the oracle's fast marching (FP64, fed the FP32-rounded speeds), FP32
 within 1e-4 max|phi|, +inf exactly.  The oracle runs on the host cores in a
 thread pool (ctypes releases the GIL).  Tomography at 192^3 with 16 shots and
 256 receivers: the adjoint gradient against central finite differences of FP64
-solves at 32 interior cells (eps 1e-3, aggregate relative error 1e-3), and the
-FP32 adjoint against the FP64 one."""
+solves at 32 interior cells (eps 1e-3, aggregate relative error 1e-3) at the
+configured initial slowness s = 1, and the FP32 adjoint against the FP64 one;
+and, for two shots, the FP64 GPU adjoint node by node against the oracle's
+adjoint on the same phi (1e-10 of max |g|)."""
 import os
 import time
 from concurrent.futures import ThreadPoolExecutor
@@ -76,7 +78,8 @@ def test_full_tomography_192_gradient():
     h, rec = t["h"], t["receivers"]
     shots = [np.array([s]) for s in t["sources"]]
     s_true = t["s_true"]
-    s0 = 1.0 + 0.5 * (s_true - 1.0)                      # a model between the start and the truth
+    s0 = np.asarray(t["s_init"], dtype=np.float64)       # the configured initial model, s = 1
+    assert np.all(s0 == 1.0)
     with _pool() as ex:
         obs = list(ex.map(lambda sh: oracle.fmm(1.0 / s_true, h, sh).reshape(-1)[rec], shots))
     rec_d = torch.as_tensor(rec).cuda()
@@ -117,3 +120,25 @@ def test_full_tomography_192_gradient():
     print(f"tomography 192^3: |adj - fd| / |fd| = {rel:.2e} over 32 cells; fp32 vs fp64 "
           f"{np.linalg.norm(g32 - g64) / np.linalg.norm(g64):.2e}")
     assert rel <= 1e-3, (adj, fd)
+
+
+def test_full_tomography_192_fp64_adjoint_vs_oracle():
+    """The 192^3 FP64 GPU adjoint of two shots (receivers on the bottom face, r = 1 there)
+    against the oracle's back substitution on the same GPU phi, node by node."""
+    import torch
+    from paper_2106_15869_b300 import api
+    t = W.tomography_3d(192)
+    h, rec = t["h"], t["receivers"]
+    F = 1.0 / np.asarray(t["s_init"], dtype=np.float64)
+    Fd = torch.as_tensor(F).cuda()
+    for s in (t["sources"][0], t["sources"][5]):
+        phi = api.solve(Fd, [int(s)], h)
+        r = torch.zeros_like(phi).reshape(-1)
+        r[torch.as_tensor(rec).cuda()] = 1.0
+        r = r.view(phi.shape)
+        got = api.adjoint(Fd, [int(s)], h, phi, r).cpu().numpy()
+        want = oracle.adjoint(F, h, [int(s)], phi.cpu().numpy(), r.cpu().numpy())
+        scale = float(np.max(np.abs(want)))
+        err = float(np.max(np.abs(got - want)))
+        assert err <= 1e-10 * scale, (s, err, scale)
+        print(f"tomography 192^3 shot {s}: fp64 adjoint vs oracle max rel err {err / scale:.2e}")

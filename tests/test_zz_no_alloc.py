@@ -4,13 +4,15 @@ It serves callers that must not allocate device memory while solving; its
 scratch is a fixed static array inside the library.  Its results must match
 the ordinary eik_solve (caller workspace) within the FP32 tolerance of the
 other parity tests, on two calls in a row (the second call reuses the array
-left behind by the first).  This file is collected last on purpose.
+left behind by the first), and the oracle's fast marching within the same
+tolerance.  This file is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2106_15869_b300 import _lib
 from paper_2106_15869_b300 import workloads as W
 
@@ -56,6 +58,9 @@ def test_noalloc_matches_workspace_solve_twice():
     for inst in (first, second):
         a, b = _solve_both(inst)
         _assert_close(a, b)
+        ref = oracle.fmm(inst.F.astype(np.float32).astype(np.float64), inst.h, inst.src_idx,
+                         np.asarray(inst.src_val, np.float32).astype(np.float64))
+        _assert_close(a, ref)
 
 
 @pytest.mark.gpu
