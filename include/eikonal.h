@@ -116,10 +116,11 @@ typedef struct {
     int32_t precision;    /* EIK_FP32 / EIK_FP64 */
     int32_t skip_remedy;  /* 1 = stop after Step 2 (ablation; the result may be wrong) */
     float order;          /* list order: 0 = default (the Step-3 and FIM lists bucketed with width
-                             4, the Step-2 lists unordered), > 0 = both loops bucketed with this
-                             width in tile-crossing times (the mean crossing time, from the mean
-                             slowness), < 0 = unordered (every listed tile visited in every
-                             iteration, the schedule of Algorithm 2 as printed) */
+                             4; the Step-2 lists bucketed too on 2D grids, unordered on 3D grids),
+                             > 0 = both loops bucketed with this width in tile-crossing times (the
+                             mean crossing time, from the mean slowness), < 0 = unordered (every
+                             listed tile visited in every iteration, the schedule of Algorithm 2
+                             as printed) */
     int32_t converge;     /* Step-2 convergence test of a tile (EIK_CONVERGE_*) */
     int32_t method;       /* EIK_METHOD_* (0 = IFIM) */
     int32_t wait_limit_us; /* bound on every device-side wait of the call (grid barriers, queue

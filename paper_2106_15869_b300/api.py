@@ -85,8 +85,9 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     (eq. 5/6 with dx, dy, dz).  Returns phi with F's shape, dtype and device
     (+inf where unreachable); with return_stats also a dict of run statistics
     (this synchronises the stream).  order: 0 = default (the Step-3 lists
-    bucketed, the Step-2 lists unordered), > 0 = both loops bucketed with this
-    width in tile-crossing times, < 0 = unordered lists (every
+    bucketed; the Step-2 lists bucketed on 2D grids, unordered on 3D grids),
+    > 0 = both loops bucketed with this width in tile-crossing times, < 0 =
+    unordered lists (every
     listed tile visited in every iteration, as Algorithm 2 is printed).
     wait_limit_us: bound on every device-side wait (0 = 2 s); a wait that runs
     out ends the launch with EIK_ERR_DEVICE and phi holding upper bounds.
