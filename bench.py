@@ -55,12 +55,16 @@ FALLBACK_HBM_GBS = 6400.0
 # k_persistent, k_unpack
 LAUNCHES_PER_SOLVE = 7
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the loop kernel
-# with the default options, from ncu captures of that kernel (summaries under profiles/);
-# reported only for those options and while the kernel sources hash to the captured version
-# (else null).  "scaled_from" names a smaller capture of the same recipe whose traffic was
-# scaled by the node count.
-MEASURED_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the loop kernel
+# with the default options, from one-pass ncu captures of that kernel on the full workload (the
+# ncu captures summarised with the profiles of this repository); reported only for those options
+# and while the kernel sources hash to the captured version (else null).
+MEASURED_TRAFFIC = {
+    "maze_512": {"hash": "95f8deeee66ee190", "bytes": 4514576128 + 1033127936},
+    "lognormal_batch64": {"hash": "95f8deeee66ee190", "bytes": 11871526912 + 1619724288},
+    "tomography_192_forward": {"hash": "95f8deeee66ee190", "bytes": 1987165184 + 461180160},
+    "tomography_192_adjoint": {"hash": "2d57b71309acc773", "bytes": 10602623744 + 664185088},
+}
 
 
 # The paper's own timings (seconds on an NVIDIA Tesla P100; Tables 1, 2, 3 and 5,
@@ -402,8 +406,8 @@ def run_ours(args, ws, rank, local):
         line["cpu_baseline"] = {"value": inst_c.n_nodes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
         if not args.no_extras:
-            line["batched"]["cpu_baseline"] = cpu_baseline_batch(8)
-            line["adjoint"]["cpu_baseline"] = cpu_baseline_tomography(8)
+            line["batched"]["cpu_baseline"] = cpu_baseline_batch(64)
+            line["adjoint"]["cpu_baseline"] = cpu_baseline_tomography(16)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -621,8 +625,9 @@ def bench_adjoint(args, dev, wsp, flush_buf):
 
 
 def cpu_baseline_batch(k: int) -> dict:
-    """The oracle's fast marching on the first k instances of the 64-instance batch, one
-    instance per host core (a thread pool; ctypes releases the GIL)."""
+    """The oracle's fast marching on the first k instances of the 64-instance batch (all of
+    them by default), one instance per host core at a time (a thread pool; ctypes releases
+    the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
     import numpy as np
     import oracle
@@ -636,7 +641,7 @@ def cpu_baseline_batch(k: int) -> dict:
     dt = time.perf_counter() - t0
     nodes = sum(i.n_nodes for i in insts)
     return {"value": nodes / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
-            "sample": f"first {k} of the 64 lognormal instances ({nodes} nodes), FMM per instance, "
+            "sample": f"{k} of the 64 lognormal instances ({nodes} nodes), FMM per instance, "
                       f"one instance per thread"}
 
 
