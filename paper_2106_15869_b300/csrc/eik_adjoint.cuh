@@ -118,11 +118,10 @@ __global__ void __launch_bounds__(kSpanThreads) k_adj_init(AdjParams<T> P) {
             const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
             f[m] = T(0); ph[m] = Num<T>::inf(); rr[m] = T(0);
             if (sp.inside(t, x, y, z)) {
-                const InstDesc &d = P.desc[sp.inst[t]];
                 const long long p = sp.at(t, x, y, z);
-                f[m] = P.F[d.in_off + p];
-                ph[m] = P.phi_in[d.out_off + p];
-                rr[m] = P.r_in[d.out_off + p];
+                f[m] = P.F[sp.in_off[t] + p];
+                ph[m] = P.phi_in[sp.out_off[t] + p];
+                rr[m] = P.r_in[sp.out_off[t] + p];
             }
         }
 #pragma unroll
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(kSpanThreads) k_adj_init(AdjParams<T> P) {
             const bool fin = ph[m] < Num<T>::inf();
             if (!fin) rr[m] = T(0);                                    // an unreachable receiver has no gradient
             if (e < total) {
-                P.tau_t[e] = f[m] > T(0) ? T(P.desc[sp.inst[t]].h) / f[m] : Num<T>::inf();
+                P.tau_t[e] = f[m] > T(0) ? T(sp.h[t]) / f[m] : Num<T>::inf();
                 P.phi_t[e] = ph[m];
                 P.lam_t[e] = T(0);
                 P.r_t[e] = rr[m];

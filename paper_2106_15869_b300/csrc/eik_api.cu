@@ -190,7 +190,7 @@ bool make_layout(int64_t B, const eik_grid *grids, const Opts &o, Layout &L, std
     L.scale_done = take(sizeof(int) * (size_t)B);
     L.tile_inst = take(4 * (size_t)tiles);
     L.tile_nb = take(4 * 8 * (size_t)tiles);
-    L.tile_fstat = take(16 * (size_t)tiles);
+    L.tile_fstat = take(8 * (size_t)tiles);
     L.tstate = take(4 * (size_t)tiles);
     L.tstamp = take(4 * (size_t)tiles);
     L.tkey = take(2 * 4 * (size_t)tiles);
@@ -357,7 +357,7 @@ int run_forward(const Layout &L, const Opts &o, char *ws, const void *F, const i
     if (P.ordered) {
         const int chunks = scale_chunks(P.B);
         k_scale<BX, BY, BZ><<<(unsigned)((long long)chunks * P.B), kScaleThreads, 0, st>>>(
-            P.desc, reinterpret_cast<const float4 *>(P.tile_fstat), P.inst_scale, P.B, chunks, P.order, P.scale_part,
+            P.desc, reinterpret_cast<const float2 *>(P.tile_fstat), P.inst_scale, P.B, chunks, P.order, P.scale_part,
             P.scale_done);
         EIK_CUDA(cudaGetLastError(), "k_scale launch");
         k_tile_scale<<<(unsigned)std::min<long long>((L.n_tiles + 255) / 256, 4096), 256, 0, st>>>(P.tile_nb, P.inst_scale,

@@ -60,11 +60,9 @@ struct InstDesc {
     int64_t acc_base;             // adjoint: tiles of the gradient blocks' first instances before this one
 };
 
-// Partial speed statistics of a slice of an instance's tiles (key-scale reduction).
+// Partial slowness statistics of a slice of an instance's tiles (key-scale reduction).
 struct ScalePart {
     double sum, cnt;
-    float mn, mx;
-    float pad[2];
 };
 
 struct DescChunk {                // by-value kernel parameter (capture-safe upload)

@@ -53,7 +53,7 @@ struct FwdParams {
     float *inst_scale;           // [B] 1/delta of each instance (ordered schedule)
     ScalePart *scale_part;       // [B][scale_chunks(B)] partial speed statistics (k_scale)
     int *scale_done;             // [B] k_scale CTAs finished per instance
-    float *tile_fstat;           // [n_tiles][4] sum of 1/F, count, min F, max F over passable nodes (delta)
+    float *tile_fstat;           // [n_tiles][2] sum of 1/F and count over passable nodes (delta)
     int ordered;                 // 1 = bucketed order of the Step-3 (and FIM) lists; keys are kept
     int ordered_update;          // 1 = bucketed order of the Step-2 lists too
     float order;                 // bucket width in tile-crossing times

@@ -66,7 +66,7 @@ __host__ __device__ constexpr int scale_chunks(long long B) { return B <= 64 ? 6
 // into part[]; the last CTA of the instance to finish (counted in done[],
 // zeroed by k_init) combines the slices and writes the key scale.
 template <int BX, int BY, int BZ>
-__global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, const float4 *tile_fstat,
+__global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, const float2 *tile_fstat,
                                                          float *inst_scale, int B, int chunks, float order,
                                                          ScalePart *part, int *done) {
     const int b = blockIdx.x / chunks, c = blockIdx.x % chunks;
@@ -76,56 +76,49 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale(const InstDesc *desc, c
     const long long per = (nt + chunks - 1) / chunks;
     const long long t_end = min(nt, (c + 1) * per);
     double sum = 0.0, cnt = 0.0;
-    float mn = __int_as_float(0x7f800000), mx = 0.0f;
     for (long long t0 = c * per + threadIdx.x; t0 < t_end; t0 += (long long)kScaleThreads * kScaleUnroll) {
-        float4 v[kScaleUnroll];
+        float2 v[kScaleUnroll];
 #pragma unroll
         for (int u = 0; u < kScaleUnroll; ++u) {
             const long long t = t0 + (long long)u * kScaleThreads;
-            v[u] = t < t_end ? __ldg(tile_fstat + d.tile_base + t) : make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+            v[u] = t < t_end ? __ldg(tile_fstat + d.tile_base + t) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kScaleUnroll; ++u) {
-            sum += v[u].x; cnt += v[u].y; mn = fminf(mn, v[u].z); mx = fmaxf(mx, v[u].w);
+            sum += v[u].x; cnt += v[u].y;
         }
     }
     __shared__ double s_sum[kScaleThreads / 32], s_cnt[kScaleThreads / 32];
-    __shared__ float s_mn[kScaleThreads / 32], s_mx[kScaleThreads / 32];
     __shared__ int s_last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_sum[w] = sum; s_cnt[w] = cnt; s_mn[w] = mn; s_mx[w] = mx; }
+    if ((threadIdx.x & 31) == 0) { s_sum[w] = sum; s_cnt[w] = cnt; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 1; q < kScaleThreads / 32; ++q) {
-            sum += s_sum[q]; cnt += s_cnt[q]; mn = fminf(mn, s_mn[q]); mx = fmaxf(mx, s_mx[q]);
+            sum += s_sum[q]; cnt += s_cnt[q];
         }
         ScalePart &p = part[(size_t)b * chunks + c];
-        p.sum = sum; p.cnt = cnt; p.mn = mn; p.mx = mx;
+        p.sum = sum; p.cnt = cnt;
         __threadfence();
         s_last = atomicAdd(done + b, 1) == chunks - 1;
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
     __threadfence();
-    sum = 0.0; cnt = 0.0; mn = __int_as_float(0x7f800000); mx = 0.0f;
+    sum = 0.0; cnt = 0.0;
     for (int q = 0; q < chunks; ++q) {
         const ScalePart &p = part[(size_t)b * chunks + q];
         sum += ld_volatile_d(&p.sum); cnt += ld_volatile_d(&p.cnt);
-        mn = fminf(mn, ld_volatile_f(&p.mn)); mx = fmaxf(mx, ld_volatile_f(&p.mx));
     }
     const double edge = BZ == 1 ? 0.5 * (BX + BY) : (BX + BY + BZ) / 3.0;
     const double mean_slow = cnt > 0 ? sum / cnt : 0.0;
     double sc = mean_slow > 0 ? 1.0 / ((double)order * edge * d.h * mean_slow) : 1.0;
     if (!(sc > 0) || !(sc < 1e30)) sc = 1.0;
-    (void)mn;
-    (void)mx;
     inst_scale[b] = (float)sc;
 }
 
@@ -139,11 +132,14 @@ template <int BX, int BY, int BZ>
 struct TileSpan {
     int inst[kSpan], l[kSpan], tc[kSpan][3], lim[kSpan][3], nx[kSpan];
     long long corner[kSpan], plane[kSpan];   // node (0, 0, 0) of the tile within its instance's grid
+    long long in_off[kSpan], out_off[kSpan]; // the instance's input and output offsets (no descriptor
+    double h[kSpan];                         // read per element), and its spacing
     // acc: g counts the tiles of the adjoint's gradient blocks (acc_base) instead of all tiles
     __device__ void fill(const InstDesc *desc, int B, long long n_tiles, long long g0, int t, bool acc = false) {
         const long long g = g0 + t;
         int b = 0, ll = 0, tx = 0, ty = 0, tz = 0, lx = 0, ly = 0, lz = 0, nxx = 0;
-        long long c = 0, pl = 0;
+        long long c = 0, pl = 0, io = 0, oo = 0;
+        double hh = 0.0;
         if (g < n_tiles) {
             b = B == 1 ? 0 : acc ? find_inst_by_acc(desc, B, g) : find_inst_by_tile(desc, B, g);
             const InstDesc &d = desc[b];
@@ -153,8 +149,12 @@ struct TileSpan {
             nxx = d.nx;
             pl = (long long)d.nx * d.ny;
             c = (long long)tz * BZ * pl + (long long)ty * BY * d.nx + (long long)tx * BX;
+            io = d.in_off;
+            oo = d.out_off;
+            hh = d.h;
         }
         inst[t] = b; l[t] = ll;
+        in_off[t] = io; out_off[t] = oo; h[t] = hh;
         tc[t][0] = tx; tc[t][1] = ty; tc[t][2] = tz;
         lim[t][0] = lx; lim[t][1] = ly; lim[t][2] = lz;
         nx[t] = nxx; plane[t] = pl; corner[t] = c;
@@ -176,14 +176,13 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
     constexpr int PER = kSpan * G::V / kSpanThreads;
     static_assert(kSpan * G::V % kSpanThreads == 0 && G::V % 32 == 0, "whole nodes per thread, whole warps per tile");
     __shared__ TileSpan<BX, BY, BZ> sp;
-    __shared__ float s_acc[kSpan][4];          // sum of the slownesses 1/F, count, min and max F (passable nodes)
+    __shared__ float s_acc[kSpan][2];          // sum of the slownesses 1/F, count (passable nodes)
     const int tid = threadIdx.x;
     const long long total = (long long)P.n_tiles * G::V;
     for (long long g0 = (long long)blockIdx.x * kSpan; g0 < P.n_tiles; g0 += (long long)gridDim.x * kSpan) {
         if (tid < kSpan) {
             sp.fill(P.desc, P.B, P.n_tiles, g0, tid);
             s_acc[tid][0] = 0.0f; s_acc[tid][1] = 0.0f;
-            s_acc[tid][2] = __int_as_float(0x7f800000); s_acc[tid][3] = 0.0f;
         }
         __syncthreads();
         T f[PER];
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
             const int r = tid + m * kSpanThreads, t = r / G::V, q = r % G::V;
             const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
             f[m] = T(0);                                    // outside the grid: tau = +inf
-            if (sp.inside(t, x, y, z)) f[m] = P.F[P.desc[sp.inst[t]].in_off + sp.at(t, x, y, z)];
+            if (sp.inside(t, x, y, z)) f[m] = P.F[sp.in_off[t] + sp.at(t, x, y, z)];
         }
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
@@ -200,25 +199,17 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
             const long long e = g0 * G::V + r;
             const bool pass = f[m] > T(0);
             if (e < total) {
-                P.tau_t[e] = pass ? T(P.desc[sp.inst[t]].h) / f[m] : Num<T>::inf();
+                P.tau_t[e] = pass ? T(sp.h[t]) / f[m] : Num<T>::inf();
                 P.phi_t[e] = Num<T>::inf();
             }
             if (P.ordered) {   // a warp's 32 nodes lie in one tile
-                const float fv = pass ? (float)f[m] : 0.0f;
-                float fs = pass ? 1.0f / fv : 0.0f, fc = pass ? 1.0f : 0.0f;
-                float fmn = pass ? fv : __int_as_float(0x7f800000), fmx = fv;
+                float fs = pass ? 1.0f / (float)f[m] : 0.0f;
+                const int fc = __popc(__ballot_sync(0xffffffffu, pass));
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    fs += __shfl_xor_sync(0xffffffffu, fs, o);
-                    fc += __shfl_xor_sync(0xffffffffu, fc, o);
-                    fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-                    fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-                }
-                if ((tid & 31) == 0) {
+                for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(0xffffffffu, fs, o);
+                if ((tid & 31) == 0 && fc) {
                     atomicAdd(&s_acc[t][0], fs);
-                    atomicAdd(&s_acc[t][1], fc);
-                    atomicMin(reinterpret_cast<int *>(&s_acc[t][2]), __float_as_int(fmn));   // non-negative floats
-                    atomicMax(reinterpret_cast<int *>(&s_acc[t][3]), __float_as_int(fmx));
+                    atomicAdd(&s_acc[t][1], (float)fc);
                 }
             }
         }
@@ -232,8 +223,7 @@ __global__ void __launch_bounds__(kSpanThreads) k_init(FwdParams<T> P) {
             P.tstamp[g] = 0;
             P.tkey[g] = kKeyInf;
             P.tkey[P.n_tiles + g] = kKeyInf;
-            if (P.ordered)
-                reinterpret_cast<float4 *>(P.tile_fstat)[g] = make_float4(s_acc[tid][0], s_acc[tid][1], s_acc[tid][2], s_acc[tid][3]);
+            if (P.ordered) reinterpret_cast<float2 *>(P.tile_fstat)[g] = make_float2(s_acc[tid][0], s_acc[tid][1]);
         }
         if (tid < 8 * kSpan && g0 + tid / 8 < P.n_tiles) {   // tile records: neighbours, instance, key scale
             const int t = tid / 8, k = tid % 8;
@@ -627,7 +617,7 @@ __global__ void __launch_bounds__(kSpanThreads) k_unpack(FwdParams<T> P) {
         for (int m = 0; m < PER; ++m) {
             const int r = threadIdx.x + m * kSpanThreads, t = r / G::V, q = r % G::V;
             const int x = q % BX, y = (q / BX) % BY, z = q / (BX * BY);
-            if (sp.inside(t, x, y, z)) P.phi_out[P.desc[sp.inst[t]].out_off + sp.at(t, x, y, z)] = val[m];
+            if (sp.inside(t, x, y, z)) P.phi_out[sp.out_off[t] + sp.at(t, x, y, z)] = val[m];
         }
         __syncthreads();                                            // the span is refilled next
     }
