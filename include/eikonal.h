@@ -140,7 +140,9 @@ typedef struct {
     int64_t sweeps;           /* in-tile relaxation sweeps, summed over visits */
     int64_t tiles_deferred;   /* listed tiles passed over by the ordered schedule */
     int32_t status;           /* EIK_* code of the device-side run */
-    int32_t device_flags;     /* bit 0 cap hit, bit 1 wait timeout, bit 2 bad source, bit 3 list overflow */
+    int32_t device_flags;     /* bit 0 cap hit, bit 1 wait timeout, bit 2 bad source, bit 3 list overflow;
+                                 checked build (libeikonal_debug.so) only: bit 4 a tile id out of range,
+                                 bit 5 a NaN written to phi or lambda (both reported as EIK_ERR_DEVICE) */
     double ms_total;          /* device time of the call, first to last kernel (CUDA events on `stream`) */
     double ms_loop;           /* device time of the Step-2/3 loop launch(es) */
 } eik_stats;
