@@ -3,8 +3,8 @@
 The best tile shape (4x4x4, 8x4x4, 8x8x4, 8x8x8; 16x16x1 or 8x8x1 in 2D),
 list order (bucketed or unordered) and schedule (the persistent kernel with
 its per-iteration list passes, or the asynchronous work queue) depend on the
-grid size, the batch size and the speed field (a strong speed contrast
-defeats the bucketed order).  tune()
+grid size, the batch size and the speed field (slow walls in a fast medium
+change which list order wins).  tune()
 times each candidate on the caller's own inputs (device time from the
 library's CUDA events, median of a few runs) and caches the winner in a JSON
 file keyed by

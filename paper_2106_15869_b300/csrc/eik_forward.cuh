@@ -51,7 +51,7 @@ struct FwdParams {
     int *tstamp;
     unsigned *tkey;              // [2][n_tiles] encoded list keys (ordered schedule)
     float *inst_scale;           // [B] 1/delta of each instance (ordered schedule)
-    ScalePart *scale_part;       // [B][scale_chunks(B)] partial speed statistics (k_scale)
+    ScalePart *scale_part;       // [B][scale_chunks(B)] partial slowness statistics (k_scale)
     int *scale_done;             // [B] k_scale CTAs finished per instance
     float *tile_fstat;           // [n_tiles][2] sum of 1/F and count over passable nodes (delta)
     int ordered;                 // 1 = bucketed order of the Step-3 (and FIM) lists; keys are kept

@@ -166,7 +166,7 @@ struct TileSpan {
 };
 
 // Step 1a: bricked tau = h/F and phi = +inf; per-tile state, neighbour ids
-// and (ordered schedule) speed statistics; control block.  A CTA takes kSpan
+// and (ordered schedule) slowness statistics; control block.  A CTA takes kSpan
 // consecutive tiles at a time: every thread loads its kSpan * V /
 // kSpanThreads speeds at once (rows of BX nodes of the caller's grid), then
 // writes the bricks (one contiguous block).
