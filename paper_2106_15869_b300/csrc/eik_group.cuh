@@ -170,6 +170,44 @@ __device__ __forceinline__ void group_fetch(const FwdParams<T> &P, GroupCtl &gc,
 template <int BX, int BY, int BZ>
 __device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>::faces_of(q); }
 
+// Face statistics of a visited tile over the nodes of the group selected by
+// `sel` (bit m: the thread's node m): the faces holding a selected node
+// (gc.fmask) and, per face, the smallest selected value as a key (gc.fmin).
+// Each thread reduces its own nodes, each warp reduces its lanes, and one
+// lane per warp updates the shared record: a handful of shared atomics per
+// visit instead of one per face node, which serialised on six addresses.
+// Every lane of the group's warps calls it.
+template <class T, int BX, int BY, int BZ, int GTM>
+__device__ __forceinline__ void group_face_stats(GroupCtl &gc, int gt, const T (&v)[GroupGeom<BX, BY, BZ, GTM>::NPT],
+                                                 unsigned sel, bool want_mask, bool want_min) {
+    using GG = GroupGeom<BX, BY, BZ, GTM>;
+    float lm[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) lm[f] = Num<float>::inf();
+    unsigned bits = 0;
+#pragma unroll
+    for (int m = 0; m < GG::NPT; ++m) {
+        if (!(sel >> m & 1)) continue;
+        const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
+        bits |= (unsigned)fb;
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            if (fb >> f & 1) lm[f] = fminf(lm[f], (float)v[m]);
+    }
+    const bool lead = lane_id() == 0;
+    if (want_mask) {
+        const unsigned b = __reduce_or_sync(kFull, bits);
+        if (lead && b) atomicOr(&gc.fmask, (int)b);
+    }
+    if (want_min) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const unsigned k = __reduce_min_sync(kFull, key_enc(lm[f]));
+            if (lead && k != kKeyInf) atomicMin(&gc.fmin[f], k);
+        }
+    }
+}
+
 // Per-group queue of the tiles a group visits from the chunk of the list it took.
 constexpr int kQueueRec = 4;                           // queued tiles whose records the classification loads
 struct GroupQueue {
@@ -227,12 +265,7 @@ __device__ __forceinline__ void visit_and_list(const FwdParams<T> &P, T *sm, Gro
         } else {
             // converged: Active -> Source, Distant face neighbours become Active
             if (ord.on) {
-#pragma unroll
-                for (int m = 0; m < GG::NPT; ++m) {
-                    const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
-                    for (int f = 0; f < 6; ++f)
-                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-                }
+                group_face_stats<T, BX, BY, BZ, GTM>(gc, gt, v, ~0u, false, true);
                 group_sync(bid, GG::GT);
             }
             if (gt < 32) {
@@ -250,17 +283,7 @@ __device__ __forceinline__ void visit_and_list(const FwdParams<T> &P, T *sm, Gro
         }
     } else {
         // faces where a node dropped, and (ordered) the smallest dropped value on each
-#pragma unroll
-        for (int m = 0; m < GG::NPT; ++m) {
-            if (!(mine >> m & 1)) continue;
-            const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
-            if (fb) {
-                atomicOr(&gc.fmask, fb);
-                if (ord.on)
-                    for (int f = 0; f < 6; ++f)
-                        if (fb >> f & 1) atomicMin(&gc.fmin[f], key_enc((float)v[m]));
-            }
-        }
+        group_face_stats<T, BX, BY, BZ, GTM>(gc, gt, v, mine, true, ord.on);
         group_sync(bid, GG::GT);
         if (gt < 32) {
             const int fm = gc.fmask;
