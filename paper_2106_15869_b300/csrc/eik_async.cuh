@@ -233,13 +233,11 @@ __device__ void async_detect_pass(const FwdParams<T> &P, const AsyncQ &Q, T *sm,
         bool low = false;
 #pragma unroll
         for (int m = 0; m < G::NPL; ++m) {
-            if (!(tau[m] < T(0))) {
-                const int c = G::sidx_of(lane + 32 * m);
-                const T ax = vmin(sm[c - 1], sm[c + 1]);
-                const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
-                const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                low |= node_solve(ax, ay, az, tau[m], P.mt) < v[m];
-            }
+            const int c = G::sidx_of(lane + 32 * m);
+            const T ax = vmin(sm[c - 1], sm[c + 1]);
+            const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
+            const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
+            low |= node_solve(ax, ay, az, tau[m], P.mt) < v[m];
         }
         if (__any_sync(kFull, low) && lane == 0) {
             st_flagged++;

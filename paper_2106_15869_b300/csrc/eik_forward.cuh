@@ -209,7 +209,7 @@ __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NP
         unsigned ch = 0;
 #pragma unroll
         for (int m = 0; m < G::NPL; ++m) {
-            if ((act >> m & 1) && !(tau[m] < T(0))) {
+            if (act >> m & 1) {
                 const int c = G::sidx_of(lane + 32 * m);
                 const T ax = vmin(sm[c - 1], sm[c + 1]);
                 const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
@@ -392,14 +392,12 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
         float kmin = __int_as_float(0x7f800000);
 #pragma unroll
         for (int m = 0; m < G::NPL; ++m) {
-            if (!(tau[m] < T(0))) {
-                const int c = G::sidx_of(lane + 32 * m);
-                const T ax = vmin(sm[c - 1], sm[c + 1]);
-                const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
-                const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = node_solve(ax, ay, az, tau[m], P.mt);
-                if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
-            }
+            const int c = G::sidx_of(lane + 32 * m);
+            const T ax = vmin(sm[c - 1], sm[c + 1]);
+            const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
+            const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
+            const T u = node_solve(ax, ay, az, tau[m], P.mt);
+            if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
         }
         const bool any = __any_sync(kFull, low);
         if (P.ordered) {

@@ -110,23 +110,21 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     for (;;) {
         unsigned ch = 0;
         auto relax = [&](int m) {
-            if (!(tau[m] < T(0))) {
-                const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
-                const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
-                // z neighbours inside the thread's own segment come from registers (no
-                // shared-memory round trip on the Gauss-Seidel chain; 1-2 % faster)
-                T zlo, zhi;
-                if constexpr (GG::ZSEG) {
-                    zlo = m > 0 ? v[m > 0 ? m - 1 : 0] : sm[c[m] - G::SX * G::SY];
-                    zhi = m + 1 < GG::NPT ? v[m + 1 < GG::NPT ? m + 1 : m] : sm[c[m] + G::SX * G::SY];
-                } else {
-                    zlo = sm[c[m] - G::SX * G::SY];
-                    zhi = sm[c[m] + G::SX * G::SY];
-                }
-                const T az = vmin(zlo, zhi);
-                const T u = node_solve(ax, ay, az, tau[m], P.mt);
-                if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
+            const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
+            const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
+            // z neighbours inside the thread's own segment come from registers (no
+            // shared-memory round trip on the Gauss-Seidel chain; 1-2 % faster)
+            T zlo, zhi;
+            if constexpr (GG::ZSEG) {
+                zlo = m > 0 ? v[m > 0 ? m - 1 : 0] : sm[c[m] - G::SX * G::SY];
+                zhi = m + 1 < GG::NPT ? v[m + 1 < GG::NPT ? m + 1 : m] : sm[c[m] + G::SX * G::SY];
+            } else {
+                zlo = sm[c[m] - G::SX * G::SY];
+                zhi = sm[c[m] + G::SX * G::SY];
             }
+            const T az = vmin(zlo, zhi);
+            const T u = node_solve(ax, ay, az, tau[m], P.mt);
+            if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
         };
         if (down) {
 #pragma unroll

@@ -275,7 +275,7 @@ __device__ __forceinline__ void atomic_min_val(double *p, double v) {
     }
 }
 
-// Step 1b: sources fixed (phi = value, tau = -1 marker); Active = the tiles
+// Step 1b: sources fixed (phi = value, tau = +inf: never lowered); Active = the tiles
 // that hold the sources' face neighbours (the source tile and, for a source on
 // a tile face, the tile across that face).
 template <class T, int BX, int BY, int BZ>
@@ -294,7 +294,7 @@ __global__ void k_sources(FwdParams<T> P) {
     const int g = (int)(d.tile_base + ((long long)tz * d.ty + ty) * d.tx + tx);
     const int loc = ((k % BZ) * BY + (j % BY)) * BX + (i % BX);
     atomic_min_val(P.phi_t + (size_t)g * G::V + loc, P.src_val[s]);
-    P.tau_t[(size_t)g * G::V + loc] = T(-1);
+    P.tau_t[(size_t)g * G::V + loc] = Num<T>::inf();
     int cand[7];
     int nc = 0;
     cand[nc++] = g;
