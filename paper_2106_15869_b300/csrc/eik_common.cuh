@@ -324,6 +324,15 @@ __device__ __forceinline__ double sweep_solve_w(double ax, double ay, double az,
 }
 
 // The root every relaxation uses: isotropic cascade, or the weighted one.
+// The same with the spacing case fixed at compile time: the sweeps of the
+// group passes select it once per visit, not once per node.
+template <bool ANISO, class T>
+__device__ __forceinline__ T node_solve_fixed(T ax, T ay, T az, T tau, const Metric<T> &mt) {
+    if constexpr (ANISO)
+        return sweep_solve_w(ax, ay, az, tau, mt);
+    else
+        return sweep_solve(ax, ay, az, tau);
+}
 template <class T>
 __device__ __forceinline__ T node_solve(T ax, T ay, T az, T tau, const Metric<T> &mt) {
     return mt.aniso ? sweep_solve_w(ax, ay, az, tau, mt) : sweep_solve(ax, ay, az, tau);

@@ -10,6 +10,8 @@
 // mode or the other for all its tiles (every CTA sees the same list size).
 #pragma once
 
+#include <type_traits>
+
 #include "eik_forward.cuh"
 
 namespace eik {
@@ -106,39 +108,44 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
     }
     mine = 0;
     first_changed = false;
-    int s = 0;
-    for (;;) {
-        unsigned ch = 0;
-        auto relax = [&](int m) {
-            const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
-            const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
-            // z neighbours inside the thread's own segment come from registers (no
-            // shared-memory round trip on the Gauss-Seidel chain; 1-2 % faster)
-            T zlo, zhi;
-            if constexpr (GG::ZSEG) {
-                zlo = m > 0 ? v[m > 0 ? m - 1 : 0] : sm[c[m] - G::SX * G::SY];
-                zhi = m + 1 < GG::NPT ? v[m + 1 < GG::NPT ? m + 1 : m] : sm[c[m] + G::SX * G::SY];
+    // the sweeps, with the spacing case (equal or unequal) fixed for the whole loop
+    auto sweep_loop = [&](auto aniso) {
+        int s = 0;
+        for (;;) {
+            unsigned ch = 0;
+            auto relax = [&](int m) {
+                const T ax = vmin(sm[c[m] - 1], sm[c[m] + 1]);
+                const T ay = vmin(sm[c[m] - G::SX], sm[c[m] + G::SX]);
+                // z neighbours inside the thread's own segment come from registers (no
+                // shared-memory round trip on the Gauss-Seidel chain; 1-2 % faster)
+                T zlo, zhi;
+                if constexpr (GG::ZSEG) {
+                    zlo = m > 0 ? v[m > 0 ? m - 1 : 0] : sm[c[m] - G::SX * G::SY];
+                    zhi = m + 1 < GG::NPT ? v[m + 1 < GG::NPT ? m + 1 : m] : sm[c[m] + G::SX * G::SY];
+                } else {
+                    zlo = sm[c[m] - G::SX * G::SY];
+                    zhi = sm[c[m] + G::SX * G::SY];
+                }
+                const T az = vmin(zlo, zhi);
+                const T u = node_solve_fixed<decltype(aniso)::value>(ax, ay, az, tau[m], P.mt);
+                if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
+            };
+            if (down) {
+#pragma unroll
+                for (int m = GG::NPT - 1; m >= 0; --m) relax(m);
             } else {
-                zlo = sm[c[m] - G::SX * G::SY];
-                zhi = sm[c[m] + G::SX * G::SY];
+#pragma unroll
+                for (int m = 0; m < GG::NPT; ++m) relax(m);
             }
-            const T az = vmin(zlo, zhi);
-            const T u = node_solve(ax, ay, az, tau[m], P.mt);
-            if (u < v[m]) { v[m] = u; sm[c[m]] = u; ch |= 1u << m; }
-        };
-        if (down) {
-#pragma unroll
-            for (int m = GG::NPT - 1; m >= 0; --m) relax(m);
-        } else {
-#pragma unroll
-            for (int m = 0; m < GG::NPT; ++m) relax(m);
+            mine |= ch;
+            ++s;
+            const int any = group_sync_or(bid, GG::GT, ch != 0);
+            if (s == 1) first_changed = any != 0;
+            if (!any || s >= P.max_sweeps) break;
         }
-        mine |= ch;
-        ++s;
-        const int any = group_sync_or(bid, GG::GT, ch != 0);
-        if (s == 1) first_changed = any != 0;
-        if (!any || s >= P.max_sweeps) break;
-    }
+        return s;
+    };
+    const int s = P.mt.aniso ? sweep_loop(std::true_type{}) : sweep_loop(std::false_type{});
 #pragma unroll
     for (int m = 0; m < GG::NPT; ++m)
         if (mine >> m & 1) {
