@@ -327,8 +327,9 @@ __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, B
     int s = 0;
     for (;;) {
         unsigned ch = 0;
+        // a node with J == 0 (a source, an unreachable or impassable node) has rJ = 0 and zero
+        // weights, so its update is 0 * (finite sum) = 0 = its lambda: no test per node
         auto relax = [&](int m) {
-            if (!(rJ[m] > T(0))) return;
             const int c = G::sidx(x[m], y[m], z[m]);
             T acc = rr[m];
             acc += w[m][0] * sm.lam[c - 1];

@@ -25,6 +25,8 @@
 
 #include <cstddef>
 
+#include <type_traits>
+
 #include "eik_common.cuh"
 
 namespace eik {
@@ -203,30 +205,34 @@ __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NP
     const int lane = lane_id();
     mine = 0;
     first_changed = false;
-    unsigned act = G::NPL >= 32 ? ~0u : ((1u << G::NPL) - 1u);
-    int s = 0;
-    for (;;) {
-        unsigned ch = 0;
+    // the sweeps, with the spacing case (equal or unequal) fixed for the whole loop
+    auto sweep_loop = [&](auto aniso) {
+        unsigned act = G::NPL >= 32 ? ~0u : ((1u << G::NPL) - 1u);
+        int s = 0;
+        for (;;) {
+            unsigned ch = 0;
 #pragma unroll
-        for (int m = 0; m < G::NPL; ++m) {
-            if (act >> m & 1) {
-                const int c = G::sidx_of(lane + 32 * m);
-                const T ax = vmin(sm[c - 1], sm[c + 1]);
-                const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
-                const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-                const T u = node_solve(ax, ay, az, tau[m], mt);
-                if (u < v[m]) { v[m] = u; sm[c] = u; ch |= 1u << m; }
+            for (int m = 0; m < G::NPL; ++m) {
+                if (act >> m & 1) {
+                    const int c = G::sidx_of(lane + 32 * m);
+                    const T ax = vmin(sm[c - 1], sm[c + 1]);
+                    const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
+                    const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
+                    const T u = node_solve_fixed<decltype(aniso)::value>(ax, ay, az, tau[m], mt);
+                    if (u < v[m]) { v[m] = u; sm[c] = u; ch |= 1u << m; }
+                }
             }
+            mine |= ch;
+            ++s;
+            __syncwarp();
+            const unsigned M = __reduce_or_sync(kFull, ch);
+            if (s == 1) first_changed = M != 0;
+            if (!M || s >= max_sweeps) break;
+            act = spread_slots<BX, BY, BZ>(M);
         }
-        mine |= ch;
-        ++s;
-        __syncwarp();
-        const unsigned M = __reduce_or_sync(kFull, ch);
-        if (s == 1) first_changed = M != 0;
-        if (!M || s >= max_sweeps) break;
-        act = spread_slots<BX, BY, BZ>(M);
-    }
-    return s;
+        return s;
+    };
+    return mt.aniso ? sweep_loop(std::true_type{}) : sweep_loop(std::false_type{});
 }
 
 // faces (bit f) holding a node that dropped in this visit, over the warp
@@ -390,15 +396,18 @@ __device__ void detect_pass(const FwdParams<T> &P, T *sm, long long &st_flagged)
         stage_tile<T, BX, BY, BZ>(P, sm, g, nbf, v, tau);
         bool low = false;
         float kmin = __int_as_float(0x7f800000);
+        auto check = [&](auto aniso) {
 #pragma unroll
-        for (int m = 0; m < G::NPL; ++m) {
-            const int c = G::sidx_of(lane + 32 * m);
-            const T ax = vmin(sm[c - 1], sm[c + 1]);
-            const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
-            const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
-            const T u = node_solve(ax, ay, az, tau[m], P.mt);
-            if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
-        }
+            for (int m = 0; m < G::NPL; ++m) {
+                const int c = G::sidx_of(lane + 32 * m);
+                const T ax = vmin(sm[c - 1], sm[c + 1]);
+                const T ay = vmin(sm[c - G::SX], sm[c + G::SX]);
+                const T az = vmin(sm[c - G::SX * G::SY], sm[c + G::SX * G::SY]);
+                const T u = node_solve_fixed<decltype(aniso)::value>(ax, ay, az, tau[m], P.mt);
+                if (u < v[m]) { low = true; kmin = fminf(kmin, (float)u); }
+            }
+        };
+        if (P.mt.aniso) check(std::true_type{}); else check(std::false_type{});
         const bool any = __any_sync(kFull, low);
         if (P.ordered) {
             const unsigned k = __reduce_min_sync(kFull, scaled_key(kmin, sc));
