@@ -48,6 +48,28 @@ struct GroupGeom {
     }
 };
 
+// Staged positions of a tile's halo elements for the group passes, one packed
+// word per element (slot in the padded block, node of the neighbour tile,
+// face): a visit reads one word per element instead of redoing the index
+// arithmetic of TileGeom::halo_of.  Filled once per launch (halo_table_fill,
+// then a CTA barrier) by every kernel that runs group passes.
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ unsigned *halo_table() {
+    __shared__ unsigned t[TileGeom<BX, BY, BZ>::HALO_LOADED];
+    return t;
+}
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ void halo_table_fill() {
+    using G = TileGeom<BX, BY, BZ>;
+    static_assert(G::S <= 2048 && G::V <= 1024, "slot and node fit their fields");
+    unsigned *t = halo_table<BX, BY, BZ>();
+    for (int h = threadIdx.x; h < G::HALO_LOADED; h += blockDim.x) {
+        int f, slot, src;
+        G::halo_of(h, f, slot, src);
+        t[h] = (unsigned)slot | (unsigned)src << 11 | (unsigned)f << 21;
+    }
+}
+
 struct GroupCtl {
     int tile;
     unsigned key;
@@ -90,10 +112,10 @@ __device__ __forceinline__ int group_visit(const FwdParams<T> &P, T *sm, const G
         c[m] = G::sidx_of(q);
         sm[c[m]] = v[m];
     }
+    const unsigned *ht = halo_table<BX, BY, BZ>();
     for (int h = gt; h < G::HALO_LOADED; h += GG::GT) {
-        int f, slot, src;
-        G::halo_of(h, f, slot, src);
-        const int n = gc.nb[f];
+        const unsigned e = ht[h];
+        const int slot = (int)(e & 2047u), src = (int)(e >> 11 & 1023u), n = gc.nb[e >> 21];
         sm[slot] = (unsigned)n < (unsigned)P.n_tiles ? __ldcg(P.phi_t + (size_t)n * G::V + src) : Num<T>::inf();
     }
     group_sync(bid, GG::GT);

@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
     __shared__ unsigned s_k;
     T *my = sm.phi[warp_in_cta()];
     init_stage<T, BX, BY, BZ>(my);
+    halo_table_fill<BX, BY, BZ>();                     // read after the loop's first CTA barrier
     if (threadIdx.x == 0) s_visits = 0;
     const int groups = gridDim.x * GroupGeom<BX, BY, BZ>::NG;
     float width = 1.0f;
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                   GroupGeom<BX, BY, BZ>::GT);
     long long t = 0, s = 0, d = 0;
     init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
+    halo_table_fill<BX, BY, BZ>();
     if (threadIdx.x == 0) s_visits = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->cnt[(it + 2) % 3] = 0;
@@ -577,6 +579,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (min_ctas<T, BX, BY, BZ>())
                                   GroupGeom<BX, BY, BZ>::GT);
     long long t = 0, s = 0, d = 0;
     init_stage<T, BX, BY, BZ>(sm.phi[warp_in_cta()]);
+    halo_table_fill<BX, BY, BZ>();
     if (threadIdx.x == 0) s_visits = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->rcnt[(r + 2) % 3] = 0;
