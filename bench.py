@@ -103,10 +103,19 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def captured_traffic(key: str, files=FORWARD_SOURCES):
-    """Bytes per launch from MEASURED_TRAFFIC for `key`, or None when absent or stale."""
+def _norm_opts(o: dict) -> tuple:
+    return (o.get("tile", "8x8x8"), float(o.get("order", 0.0)), o.get("schedule", "persistent"),
+            o.get("converge", "auto"))
+
+
+def captured_traffic(key: str, files=FORWARD_SOURCES, opts: dict | None = None):
+    """Bytes per launch from MEASURED_TRAFFIC for `key`, or None when absent or stale: the kernel
+    sources must hash to the captured version, and the solve options (default ones unless the
+    entry names others) must be the captured ones."""
     t = MEASURED_TRAFFIC.get(key)
     if not t or t.get("hash") != kernel_source_hash(files):
+        return None
+    if _norm_opts(opts or {}) != _norm_opts(t.get("opts", {})):
         return None
     return t["bytes"]
 
@@ -612,8 +621,6 @@ def bench_batched(args, dev, wsp, flush_buf):
         st = bs.stats()
         loops.append(st["ms_loop"])
     loop_ms = statistics.median(loops)
-    default = all(v == d for v, d in ((opts.get("tile"), "8x8x8"), (opts.get("order"), 0.0),
-                                      (opts.get("schedule"), "persistent")))
     return {"workload": "lognormal_batch64 (64 instances, edges 64..192, F = exp(0.3 g))", "nodes": n,
             "tuned_options": opts, "tuning_ms": tuned.get("_ms"), "tuning_s": tune_s, "graph_replay": True,
             "batched_ms": tb, "batched_nodes_per_s": n / (tb / 1e3), "plain_loop_ms": tp,
@@ -621,7 +628,7 @@ def bench_batched(args, dev, wsp, flush_buf):
             "solver_stats": {k: st[k] for k in ("iters_update", "iters_remedy", "tiles_update", "tiles_flagged",
                                                 "tiles_remedy", "sweeps")},
             "roofline": roofline_block(f"k_persistent (Steps 2-3, batch of 64, {opts})", LOOP_BYTES_PER_NODE, n,
-                                       loop_ms, captured_traffic("lognormal_batch64") if default else None,
+                                       loop_ms, captured_traffic("lognormal_batch64", opts=opts),
                                        loop_share_of_step=loop_ms / tb)}
 
 

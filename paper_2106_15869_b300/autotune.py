@@ -1,10 +1,14 @@
-"""Autotuner for the tile shape, the list order and the schedule of the solve.
+"""Autotuner for the tile shape, the list order, the schedule and the Step-2
+convergence test of the solve.
 
 The best tile shape (4x4x4, 8x4x4, 8x8x4, 8x8x8; 16x16x1 or 8x8x1 in 2D),
-list order (bucketed or unordered) and schedule (the persistent kernel with
-its per-iteration list passes, or the asynchronous work queue) depend on the
-grid size, the batch size and the speed field (slow walls in a fast medium
-change which list order wins).  tune()
+list order (bucketed or unordered), schedule (the persistent kernel with
+its per-iteration list passes, or the asynchronous work queue) and Step-2
+convergence test of a tile (a confirming visit that changes nothing, or the
+visit's own relaxation reaching the tile's fixed point) depend on the grid
+size, the batch size and the speed field (slow walls in a fast medium change
+which list order wins; smooth speeds from one corner favour the one-visit
+test, many sources on a face the confirming one).  tune()
 times each candidate on the caller's own inputs (device time from the
 library's CUDA events, median of a few runs) and caches the winner in a JSON
 file keyed by
@@ -28,9 +32,12 @@ import torch
 
 from . import api
 
-# persistent schedule with either list order, and the asynchronous queue (which has no order)
+# persistent schedule with either list order, and the asynchronous queue (which has no order); on
+# 8x8x8 tiles also the one-visit Step-2 test (measured on B300: 14 % faster on the 256^3
+# oscillating speed and 3 % on the 64-instance lognormal batch, 2x slower on the 16-shot tomography)
 CANDIDATES_3D = ([dict(tile=t, order=o, schedule="persistent") for t in ("8x8x4", "8x4x4", "4x4x4", "8x8x8")
-                  for o in (0.0, -1.0)] + [dict(tile=t, order=-1.0, schedule="async") for t in ("8x8x4", "8x8x8")])
+                  for o in (0.0, -1.0)] + [dict(tile=t, order=-1.0, schedule="async") for t in ("8x8x4", "8x8x8")]
+                 + [dict(tile="8x8x8", order=0.0, schedule="persistent", converge="sweep")])
 CANDIDATES_2D = ([dict(tile=t, order=o, schedule="persistent") for t in ("16x16x1", "8x8x1") for o in (0.0, -1.0)]
                  + [dict(tile="16x16x1", order=-1.0, schedule="async")])
 
@@ -84,7 +91,7 @@ def _time_solve(problems, opts, reps):
 
 
 def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=None, force: bool = False) -> dict:
-    """Options (tile, order, schedule) for this problem class, timed on `problems` on a cache miss.
+    """Options (tile, order, schedule, converge) for this problem class, timed on `problems` on a cache miss.
 
     problems: a list of (F, src_idx, h) tuples (one for a single solve) on a CUDA
     device.  Returns a dict usable as keyword arguments of api.solve /
@@ -107,7 +114,10 @@ def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=N
             t = _time_solve(problems, c, reps)
         except api._lib.EikonalError:
             continue
-        timings[f"{c['tile']}/order={c['order']}/{c.get('schedule', 'auto')}"] = t
+        name = f"{c['tile']}/order={c['order']}/{c.get('schedule', 'auto')}"
+        if c.get("converge", "auto") != "auto":
+            name += f"/converge={c['converge']}"
+        timings[name] = t
         if t < best_ms:
             best, best_ms = c, t
     if best is None:

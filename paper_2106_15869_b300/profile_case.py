@@ -1,6 +1,6 @@
 """Run one named workload a fixed number of times, for a profiler to capture.
 
-    python -m paper_2106_15869_b300.profile_case CASE [--calls N] [--stats]
+    python -m paper_2106_15869_b300.profile_case CASE [--calls N] [--stats] [--converge auto|confirm|sweep]
 
 The cases are the benchmark workloads and smaller cases built by the same
 recipes (for captures that replay a kernel many times, which want a few GB on
@@ -28,18 +28,18 @@ import torch
 from . import api, workloads as W
 
 
-def _single(inst, dev):
+def _single(inst, dev, **kw):
     F = torch.as_tensor(inst.F, dtype=torch.float32).to(dev)
     val = torch.as_tensor(inst.src_val, dtype=torch.float32).to(dev)
     ws = api.Workspace(dev)
     phi = torch.empty_like(F)
-    return lambda stats: api.solve(F, inst.src_idx, inst.h, val, workspace=ws, out=phi, return_stats=stats)
+    return lambda stats: api.solve(F, inst.src_idx, inst.h, val, workspace=ws, out=phi, return_stats=stats, **kw)
 
 
-def _batch(insts, dev):
+def _batch(insts, dev, **kw):
     probs = [(torch.as_tensor(i.F, dtype=torch.float32).to(dev), i.src_idx, i.h) for i in insts]
     ws = api.Workspace(dev)
-    return lambda stats: api.solve_batched(probs, workspace=ws, return_stats=stats)
+    return lambda stats: api.solve_batched(probs, workspace=ws, return_stats=stats, **kw)
 
 
 def _tomo(dev, shots: int, adjoint: bool):
@@ -60,17 +60,17 @@ def _tomo(dev, shots: int, adjoint: bool):
                                              return_stats=stats)
 
 
-def make_case(name: str, dev):
+def make_case(name: str, dev, converge: str = "auto"):
     if name == "maze_512":
-        return _single(W.maze_3d(512), dev)
+        return _single(W.maze_3d(512), dev, converge=converge)
     if name == "maze_256":
-        return _single(W.maze_3d(256, n_slabs=8), dev)
+        return _single(W.maze_3d(256, n_slabs=8), dev, converge=converge)
     if name == "oscillating_256":
-        return _single(W.oscillating_3d(256), dev)
+        return _single(W.oscillating_3d(256), dev, converge=converge)
     if name == "batch64":
-        return _batch(W.lognormal_batch(64), dev)
+        return _batch(W.lognormal_batch(64), dev, converge=converge)
     if name == "batch16":
-        return _batch(W.lognormal_batch(64)[:16], dev)
+        return _batch(W.lognormal_batch(64)[:16], dev, converge=converge)
     if name == "tomo192_forward":
         return _tomo(dev, 16, False)
     if name == "tomo192_adjoint":
@@ -85,9 +85,11 @@ def main():
     ap.add_argument("case")
     ap.add_argument("--calls", type=int, default=3)
     ap.add_argument("--stats", action="store_true")
+    ap.add_argument("--converge", default="auto", choices=["auto", "confirm", "sweep"],
+                    help="Step-2 convergence test of the forward cases (the tomography keeps the default)")
     a = ap.parse_args()
     dev = torch.device("cuda", torch.cuda.current_device())
-    run = make_case(a.case, dev)
+    run = make_case(a.case, dev, a.converge)
     for q in range(a.calls):
         out = run(a.stats)
         if a.stats:

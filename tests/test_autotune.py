@@ -30,6 +30,8 @@ def test_tune_caches_and_solves(tmp_path):
     opts = autotune.tune([(F, inst.src_idx, inst.h)], cache_path=path, reps=1)
     assert opts["schedule"] in ("persistent", "async")
     assert opts["tile"] in ("8x8x4", "8x4x4", "4x4x4", "8x8x8") and len(opts["_ms"]) >= 4
+    assert opts.get("converge", "auto") in ("auto", "sweep")
+    assert any("converge=sweep" in k for k in opts["_ms"])
     cached = json.load(open(path))
     assert autotune.problem_key(F) in cached
     again = autotune.tune([(F, inst.src_idx, inst.h)], cache_path=path)      # cache hit, no timing

@@ -38,3 +38,16 @@ def test_measured_peak_is_used_when_present():
         assert kind == "measured" and peak > 1000.0
     else:
         assert kind == "fallback" and peak == bench.FALLBACK_HBM_GBS
+
+
+def test_captured_traffic_needs_the_captured_options(monkeypatch):
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {
+        "default": {"hash": h, "bytes": 1},
+        "tuned": {"hash": h, "bytes": 2, "opts": {"tile": "8x8x8", "order": 0.0, "converge": "sweep"}}})
+    assert bench.captured_traffic("default") == 1
+    assert bench.captured_traffic("default", opts={"tile": "8x8x8", "order": 0.0, "schedule": "persistent"}) == 1
+    assert bench.captured_traffic("default", opts={"tile": "8x8x4"}) is None
+    assert bench.captured_traffic("tuned", opts={"tile": "8x8x8", "order": 0.0, "schedule": "persistent",
+                                                 "converge": "sweep"}) == 2
+    assert bench.captured_traffic("tuned", opts={"tile": "8x8x8", "order": 0.0}) is None
