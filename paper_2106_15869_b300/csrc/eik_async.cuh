@@ -207,7 +207,7 @@ __device__ void async_remedy_phase(const FwdParams<T> &P, const AsyncQ &Q, T *sm
         write_back<T, BX, BY, BZ>(P, g, mine, v);
         __threadfence();
         __syncwarp();
-        const int fm = changed_faces<BX, BY, BZ>(mine);
+        const int fm = lowering_faces<T, BX, BY, BZ>(mine, v, sm);
         if (lane == 0) { st_tiles++; st_sweeps += s; }
         if (lane < 6 && (fm >> lane & 1) && nbf >= 0) q_request(ctl, Q, nbf);
         if (lane == 6 && changed && s >= P.max_sweeps) q_request(ctl, Q, g);

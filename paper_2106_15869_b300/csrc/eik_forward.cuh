@@ -246,6 +246,42 @@ __device__ __forceinline__ int changed_faces(unsigned mine) {
     return (int)__reduce_or_sync(kFull, (unsigned)f);
 }
 
+// Step-3 listing test.  A node p of a tile that dropped to value u can lower
+// the node q across face f of the neighbour tile only if u < phi(q): otherwise
+// the term ((phi - u)^+)^2 of q's eq. (6) stays 0 at phi(q), so q's root
+// cannot fall below phi(q) (a neighbour tile at its fixed point stays there;
+// one that is not is listed already by whatever moved it).  The staged halo
+// holds phi(q) as it was when the visit began, never below its current value,
+// so the test can only list more.  Of fb (the faces of the node at staged slot
+// c), the faces across which value u lies below the halo.
+template <class T, int BX, int BY, int BZ>
+__device__ __forceinline__ int below_halo(const T *sm, int c, T u, int fb) {
+    using G = TileGeom<BX, BY, BZ>;
+    int r = 0;
+    if ((fb & 1) && u < sm[c - 1]) r |= 1;
+    if ((fb & 2) && u < sm[c + 1]) r |= 2;
+    if ((fb & 4) && u < sm[c - G::SX]) r |= 4;
+    if ((fb & 8) && u < sm[c + G::SX]) r |= 8;
+    if ((fb & 16) && u < sm[c - G::SX * G::SY]) r |= 16;
+    if ((fb & 32) && u < sm[c + G::SX * G::SY]) r |= 32;
+    return r;
+}
+
+// Faces across which a dropped node of the warp's tile (bit m of `mine`:
+// node lane + 32 m) lies below the staged halo (below_halo), warp-reduced.
+template <class T, int BX, int BY, int BZ>
+__device__ __forceinline__ int lowering_faces(unsigned mine, const T (&v)[TileGeom<BX, BY, BZ>::NPL], const T *sm) {
+    using G = TileGeom<BX, BY, BZ>;
+    int f = 0;
+#pragma unroll
+    for (int m = 0; m < G::NPL; ++m)
+        if (mine >> m & 1) {
+            const int q = lane_id() + 32 * m;
+            f |= below_halo<T, BX, BY, BZ>(sm, G::sidx_of(q), v[m], G::faces_of(q));
+        }
+    return (int)__reduce_or_sync(kFull, (unsigned)f);
+}
+
 template <class T, int BX, int BY, int BZ>
 __device__ __forceinline__ void write_back(const FwdParams<T> &P, int g, unsigned mine,
                                            const T (&v)[TileGeom<BX, BY, BZ>::NPL]) {
@@ -299,14 +335,20 @@ __device__ __forceinline__ bool order_visit(const OrderCtx &o, unsigned key) {
 // warp min of one float per lane, encoded
 __device__ __forceinline__ unsigned warp_min_key(float k) { return __reduce_min_sync(kFull, key_enc(k)); }
 
-// per-face minimum over this lane's nodes selected by `sel`, for face f
+// per-face minimum over this lane's nodes selected by `sel`, for face f; with
+// a staged block `sm`, only over the nodes below the halo across f (below_halo)
 template <class T, int BX, int BY, int BZ>
-__device__ __forceinline__ float face_min(unsigned sel, const T (&v)[TileGeom<BX, BY, BZ>::NPL], int f) {
+__device__ __forceinline__ float face_min(unsigned sel, const T (&v)[TileGeom<BX, BY, BZ>::NPL], int f,
+                                          const T *sm = nullptr) {
     using G = TileGeom<BX, BY, BZ>;
     float m = __int_as_float(0x7f800000);
 #pragma unroll
-    for (int q = 0; q < G::NPL; ++q)
-        if ((sel >> q & 1) && (G::faces_of(lane_id() + 32 * q) >> f & 1)) m = fminf(m, (float)v[q]);
+    for (int q = 0; q < G::NPL; ++q) {
+        const int n = lane_id() + 32 * q;
+        if (!(sel >> q & 1) || !(G::faces_of(n) >> f & 1)) continue;
+        if (sm && !below_halo<T, BX, BY, BZ>(sm, G::sidx_of(n), v[q], 1 << f)) continue;
+        m = fminf(m, (float)v[q]);
+    }
     return m;
 }
 
@@ -468,12 +510,13 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
         bool changed;
         const int s = relax_tile<T, BX, BY, BZ>(sm, v, tau, P.max_sweeps, P.mt, mine, changed);
         write_back<T, BX, BY, BZ>(P, g, mine, v);
-        const int fm = changed_faces<BX, BY, BZ>(mine);
+        const int fm = lowering_faces<T, BX, BY, BZ>(mine, v, sm);
         if (lane == 0) { st_tiles++; st_sweeps += s; atomicAdd(s_visits, 1); }
         // The tile is relaxed to its local fixed point; a neighbour whose facing
         // boundary drops re-lists it.  Lanes 0-5 list the neighbour across face
-        // `lane` when a node on that face dropped; lane 6 re-lists the tile
-        // itself when the sweep cap stopped the relaxation early.
+        // `lane` when a node on that face dropped below the node across it;
+        // lane 6 re-lists the tile itself when the sweep cap stopped the
+        // relaxation early.
         int cand = -1;
         if (lane < 6 && (fm >> lane & 1) && (unsigned)nbf < (unsigned)P.n_tiles) cand = nbf;
         if (lane == 6 && changed && s >= P.max_sweeps) cand = g;
@@ -483,7 +526,7 @@ __device__ void remedy_pass(const FwdParams<T> &P, T *sm, int r, int n, unsigned
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 if (!(fm >> f & 1)) continue;                     // warp-uniform
-                const unsigned k = __reduce_min_sync(kFull, key_enc(face_min<T, BX, BY, BZ>(mine, v, f)));
+                const unsigned k = __reduce_min_sync(kFull, key_enc(face_min<T, BX, BY, BZ>(mine, v, f, sm)));
                 if (lane == f) dm = key_dec(k);
             }
             kc = lane == 6 ? key : scaled_key(dm, sc);

@@ -200,13 +200,16 @@ __device__ __forceinline__ int node_faces_q(int q) { return TileGeom<BX, BY, BZ>
 // Face statistics of a visited tile over the nodes of the group selected by
 // `sel` (bit m: the thread's node m): the faces holding a selected node
 // (gc.fmask) and, per face, the smallest selected value as a key (gc.fmin).
-// Each thread reduces its own nodes, each warp reduces its lanes, and one
-// lane per warp updates the shared record: a handful of shared atomics per
-// visit instead of one per face node, which serialised on six addresses.
-// Every lane of the group's warps calls it.
+// With the staged block `sm` (Step 3), a node counts for a face only if it
+// lies below the halo value across it (below_halo).  Each thread reduces its
+// own nodes, each warp reduces its lanes, and one lane per warp updates the
+// shared record: a handful of shared atomics per visit instead of one per
+// face node, which serialised on six addresses.  Every lane of the group's
+// warps calls it.
 template <class T, int BX, int BY, int BZ, int GTM>
 __device__ __forceinline__ void group_face_stats(GroupCtl &gc, int gt, const T (&v)[GroupGeom<BX, BY, BZ, GTM>::NPT],
-                                                 unsigned sel, bool want_mask, bool want_min) {
+                                                 unsigned sel, bool want_mask, bool want_min,
+                                                 const T *sm = nullptr) {
     using GG = GroupGeom<BX, BY, BZ, GTM>;
     float lm[6];
 #pragma unroll
@@ -215,7 +218,9 @@ __device__ __forceinline__ void group_face_stats(GroupCtl &gc, int gt, const T (
 #pragma unroll
     for (int m = 0; m < GG::NPT; ++m) {
         if (!(sel >> m & 1)) continue;
-        const int fb = node_faces_q<BX, BY, BZ>(GG::node(gt, m));
+        const int q = GG::node(gt, m);
+        int fb = node_faces_q<BX, BY, BZ>(q);
+        if (sm) fb = below_halo<T, BX, BY, BZ>(sm, TileGeom<BX, BY, BZ>::sidx_of(q), v[m], fb);
         bits |= (unsigned)fb;
 #pragma unroll
         for (int f = 0; f < 6; ++f)
@@ -309,8 +314,8 @@ __device__ __forceinline__ void visit_and_list(const FwdParams<T> &P, T *sm, Gro
             }
         }
     } else {
-        // faces where a node dropped, and (ordered) the smallest dropped value on each
-        group_face_stats<T, BX, BY, BZ, GTM>(gc, gt, v, mine, true, ord.on);
+        // faces where a node dropped below the node across, and (ordered) the smallest such value on each
+        group_face_stats<T, BX, BY, BZ, GTM>(gc, gt, v, mine, true, ord.on, sm);
         group_sync(bid, GG::GT);
         if (gt < 32) {
             const int fm = gc.fmask;
