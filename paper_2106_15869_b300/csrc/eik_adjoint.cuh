@@ -231,6 +231,30 @@ __global__ void k_adj_sources(AdjParams<T> P) {
     P.tau_t[(size_t)g * G::V + loc] = T(-1);
 }
 
+// Faces (of fb, the faces of node (x, y, z)) across which the node's lambda
+// feeds the node beyond: node p enters the row of its neighbour q across a
+// face of the transposed system only if p selects q as its upwind neighbour on
+// that axis (q the smaller of p's two neighbours there, a tie to the lower
+// index, and phi_p > phi_q); otherwise w_{p->q} = 0 and a change of lambda_p
+// leaves q's equation as it was, so the tile beyond need not be listed for it.
+// phi is fixed during the adjoint, so the test is exact.
+template <class T, int BX, int BY, int BZ>
+__device__ __forceinline__ int adj_feeds(const T *phi, int x, int y, int z, int fb) {
+    using A = AdjGeom<BX, BY, BZ>;
+    const T pj = phi[A::pidx(x, y, z)];
+    int r = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!(fb >> (2 * ax) & 3)) continue;
+        const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+        const T lo = phi[A::pidx(x - ex, y - ey, z - ez)];
+        const T hi = phi[A::pidx(x + ex, y + ey, z + ez)];
+        if ((fb >> (2 * ax) & 1) && lo <= hi && lo < pj) r |= 1 << (2 * ax);
+        if ((fb >> (2 * ax + 1) & 1) && hi < lo && hi < pj) r |= 2 << (2 * ax);
+    }
+    return r;
+}
+
 // One visit of tile g by a group of GT threads (one or two nodes each).
 template <class T, int BX, int BY, int BZ>
 __device__ __forceinline__ int adj_visit(const AdjParams<T> &P, AdjSmem<T, BX, BY, BZ> &sm, const int (&nb)[6], int g,
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
         int *out = (r & 1) ? P.list0 : P.list1;
         const int next_stamp = r + 2;
         // Visit of tile g (its neighbours in s_nb[gi]) and the listing of the neighbour
-        // tiles across faces where lambda changed.
+        // tiles across faces where a changed lambda feeds the node beyond (adj_feeds).
         auto visit = [&](int g) {
             int nb[6];
 #pragma unroll
@@ -427,7 +451,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (sizeof(T) == 8 ? 2 : 3)) k
 #pragma unroll
             for (int m = 0; m < GG::NPT; ++m)
                 if (mine >> m & 1) {
-                    const int fb = G::faces_of(GG::node(gt, m));
+                    const int q = GG::node(gt, m);
+                    int fb = G::faces_of(q);
+                    if (fb) fb = adj_feeds<T, BX, BY, BZ>(sm.phi, q % BX, (q / BX) % BY, q / (BX * BY), fb);
                     if (fb) atomicOr(&s_fmask[gi], fb);
                 }
             group_sync(bid, GG::GT);
