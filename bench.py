@@ -56,14 +56,18 @@ FALLBACK_HBM_GBS = 6400.0
 LAUNCHES_PER_SOLVE = 7
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the loop kernel
-# with the default options, from one-pass ncu captures of that kernel on the full workload (the
-# ncu captures summarised with the profiles of this repository); reported only for those options
-# and while the kernel sources hash to the captured version (else null).
+# with the default options (or the ones an entry names), from one-pass ncu captures of that kernel
+# on the full workload (the ncu captures summarised with the profiles of this repository);
+# reported only for those options and while the kernel sources hash to the captured version
+# (else null).
 MEASURED_TRAFFIC = {
-    "maze_512": {"hash": "56e19930f3ebc148", "bytes": 4534542080 + 1040388608},
-    "lognormal_batch64": {"hash": "56e19930f3ebc148", "bytes": 11601441280 + 1625766656},
-    "tomography_192_forward": {"hash": "56e19930f3ebc148", "bytes": 1985554944 + 461356032},
-    "tomography_192_adjoint": {"hash": "d4df70ca9d53b50f", "bytes": 10439939072 + 653908736},
+    "maze_512": {"hash": "e55ecc5be9ec9032", "bytes": 3537852672 + 928447744},
+    "lognormal_batch64": {"hash": "e55ecc5be9ec9032", "bytes": 8564101120 + 1530199808},
+    "lognormal_batch64_sweep": {"hash": "e55ecc5be9ec9032", "bytes": 8236797696 + 1666992896,
+                                "opts": {"tile": "8x8x8", "order": 0.0, "schedule": "persistent",
+                                         "converge": "sweep"}},
+    "tomography_192_forward": {"hash": "e55ecc5be9ec9032", "bytes": 1980427008 + 461205504},
+    "tomography_192_adjoint": {"hash": "3bd044474a35bf45", "bytes": 4991831040 + 617165056},
 }
 
 
@@ -628,7 +632,8 @@ def bench_batched(args, dev, wsp, flush_buf):
             "solver_stats": {k: st[k] for k in ("iters_update", "iters_remedy", "tiles_update", "tiles_flagged",
                                                 "tiles_remedy", "sweeps")},
             "roofline": roofline_block(f"k_persistent (Steps 2-3, batch of 64, {opts})", LOOP_BYTES_PER_NODE, n,
-                                       loop_ms, captured_traffic("lognormal_batch64", opts=opts),
+                                       loop_ms, captured_traffic("lognormal_batch64", opts=opts)
+                                       or captured_traffic("lognormal_batch64_sweep", opts=opts),
                                        loop_share_of_step=loop_ms / tb)}
 
 
