@@ -474,11 +474,15 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     const int next_stamp = it + 2;
     const OrderCtx ord = order_begin(remedy ? P.ordered : P.ordered_update, kmin_cur, width);
     n = min(n, P.n_tiles);
+    // An unordered list keeps every entry (its entries are distinct: Step-2 lists by tile state,
+    // Step-3 lists by stamp): the groups take the entries themselves, with no classification, no
+    // visit list and no grid barrier before the visits.
+    const bool direct = !ord.on;
     // classify: a warp takes 32 consecutive entries (warp-uniform loop, every lane takes part in the
     // pushes); a kept tile goes to the visit list with its key and record
     const int lane = lane_id();
     const int nthreads = gridDim.x * blockDim.x;
-    for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += nthreads) {
+    for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); !direct && e0 < n; e0 += nthreads) {
         const int e = e0 + lane;
         bool valid = e < n;
         const int g = valid ? __ldcg(in + e) : -1;
@@ -503,7 +507,7 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
         warp_push(ctl, cnt_next, out, P.n_tiles, want, g, ord.on ? kmin_next : nullptr, key);
         push_visit(ctl, vcnt, P.vlist, P.n_tiles, valid && !defer, g, key, r0, r1);
     }
-    if (!grid_sync(ctl, target, P.wait_ns)) return false;
+    if (!direct && !grid_sync(ctl, target, P.wait_ns)) return false;
     // visit the kept tiles
     const int tid = threadIdx.x;
     const int gi = tid / GG::GT, gt = tid % GG::GT, bid = 1 + gi;
@@ -511,11 +515,15 @@ __device__ bool group_pass_split(const FwdParams<T> &P, T *smbase, GroupCtl *gcs
     GroupCtl &gc = gcs[gi];
     const int cta_groups = blockDim.x / GG::GT;
     const int groups = gridDim.x * cta_groups;
-    const int nv = min(ld_volatile(vcnt), P.n_tiles);
+    const int nv = direct ? n : min(ld_volatile(vcnt), P.n_tiles);
     for (bool first = true;; first = false) {
         if (gt == 0) {
             const int idx = first ? blockIdx.x * cta_groups + gi : groups + atomicAdd(vgrab, 1);
-            if (idx < nv) {
+            if (idx < nv && direct) {
+                const int g = __ldcg(in + idx);
+                if (dbg_bad_tile(ctl, g, P.n_tiles)) gc.tile = -1;
+                else group_fetch(P, gc, g, kKeyInf);
+            } else if (idx < nv) {
                 const VisitRec *vr = P.vlist + idx;
                 const int4 h = __ldcg(&vr->head);
                 group_set(gc, h.x, (unsigned)h.y, __ldcg(&vr->r0), __ldcg(&vr->r1));
