@@ -109,7 +109,7 @@ def measured_peaks():
 
 def _norm_opts(o: dict) -> tuple:
     return (o.get("tile", "8x8x8"), float(o.get("order", 0.0)), o.get("schedule", "persistent"),
-            o.get("converge", "auto"))
+            o.get("converge", "auto"), float(o.get("remedy_order", 0.0)))
 
 
 def captured_traffic(key: str, files=FORWARD_SOURCES, opts: dict | None = None):

@@ -128,6 +128,12 @@ typedef struct {
                               raises device flag bit 1, every thread block leaves the launch, phi
                               keeps valid upper bounds and the call reports EIK_ERR_DEVICE.  < 0 is
                               EIK_ERR_ARG. */
+    float remedy_order;   /* the Step-3 (and FIM) list order alone, where the Step-2 lists are
+                             unordered (3D grids with order 0, or order < 0): 0 = as `order` sets
+                             it, > 0 = bucketed with this width, < 0 = unordered.  Ignored when the
+                             Step-2 lists are bucketed.  Any order gives the same solution; the
+                             fastest width depends on the problem (autotune.py tries some).  The
+                             adjoint's width comes from `order` alone (0 = its default, 2). */
 } eik_options;
 
 /* run statistics (filled when a stats pointer is passed; the call then synchronises) */

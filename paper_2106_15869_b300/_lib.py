@@ -35,7 +35,8 @@ class eik_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("skip_remedy", ctypes.c_int32), ("order", ctypes.c_float),
-                ("converge", ctypes.c_int32), ("method", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
+                ("converge", ctypes.c_int32), ("method", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("remedy_order", ctypes.c_float)]
 
 
 class eik_stats(ctypes.Structure):
@@ -140,7 +141,8 @@ def check(rc: int, lib=None):
 
 
 def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=False,
-                 max_iters=0, order=0.0, converge="auto", method="ifim", wait_limit_us=0) -> eik_options:
+                 max_iters=0, order=0.0, converge="auto", method="ifim", wait_limit_us=0,
+                 remedy_order=0.0) -> eik_options:
     o = eik_options()
     o.tile = TILES[tile] if isinstance(tile, str) else int(tile)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -151,6 +153,7 @@ def make_options(tile="auto", schedule="auto", precision="fp32", skip_remedy=Fal
     o.converge = CONVERGE[converge] if isinstance(converge, str) else int(converge)
     o.method = METHODS[method] if isinstance(method, str) else int(method)
     o.wait_limit_us = int(wait_limit_us)
+    o.remedy_order = float(remedy_order)
     return o
 
 

@@ -76,7 +76,8 @@ def _workspace(device, nbytes, ws: Workspace | None):
 
 def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", schedule="auto",
           skip_remedy=False, max_iters=0, order=0.0, converge="auto", method="ifim", return_stats=False,
-          workspace: Workspace | None = None, out: torch.Tensor | None = None, wait_limit_us: int = 0):
+          workspace: Workspace | None = None, out: torch.Tensor | None = None, wait_limit_us: int = 0,
+          remedy_order: float = 0.0):
     """Arrival times phi of ||grad phi|| = 1/F with fixed values at the sources.
 
     F: (ny, nx) or (nz, ny, nx) float32 (or float64 = FP64 validation mode)
@@ -89,6 +90,9 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     > 0 = both loops bucketed with this width in tile-crossing times, < 0 =
     unordered lists (every
     listed tile visited in every iteration, as Algorithm 2 is printed).
+    remedy_order: the Step-3 list order alone where the Step-2 lists are
+    unordered (0 = as `order` sets it, > 0 = this bucket width, < 0 =
+    unordered); every order gives the same solution.
     wait_limit_us: bound on every device-side wait (0 = 2 s); a wait that runs
     out ends the launch with EIK_ERR_DEVICE and phi holding upper bounds.
     method: "ifim" (Algorithm 2: Step 2 without neighbour checks, then the
@@ -107,7 +111,7 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
     lib = _lib.load()
     g = _lib.grids_array([(nx, ny, nz, h)])
     opt = _lib.make_options(tile, schedule, _DT[Fd.dtype], skip_remedy, max_iters, order, converge, method,
-                            wait_limit_us)
+                            wait_limit_us, remedy_order)
     nbytes = lib.eik_workspace_size(g, ctypes.byref(opt))
     if nbytes == 0:
         raise _lib.EikonalError(_lib.EIK_ERR_ARG, "invalid grid or options")
@@ -127,13 +131,14 @@ def solve(F: torch.Tensor, src_idx, h: float, src_val=None, *, tile="auto", sche
 
 def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, max_iters=0, order=0.0,
                   converge="auto", method="ifim", return_stats=False, workspace: Workspace | None = None,
-                  shared_F: bool = False, wait_limit_us: int = 0):
+                  shared_F: bool = False, wait_limit_us: int = 0, remedy_order: float = 0.0):
     """Solve many independent grids in one set of launches.
 
     problems: list of (F, src_idx, h) or (F, src_idx, h, src_val); all F on the
     same CUDA device with the same dtype.  With shared_F=True every problem
     uses the first problem's F (one copy, read by all instances; e.g. many
-    sources on one speed map).  Returns a list of phi tensors.
+    sources on one speed map).  Options as for solve().  Returns a list of phi
+    tensors.
     """
     if not problems:
         return ([], {}) if return_stats else []
@@ -170,7 +175,7 @@ def solve_batched(problems, *, tile="auto", schedule="auto", skip_remedy=False, 
     lib = _lib.load()
     g = _lib.grids_array(dims)
     opt = _lib.make_options(tile, schedule, _DT[dtype], skip_remedy, max_iters, order, converge, method,
-                            wait_limit_us)
+                            wait_limit_us, remedy_order)
     B = len(problems)
     nbytes = lib.eik_workspace_size_batched(B, g, ctypes.byref(opt))
     if nbytes == 0:
@@ -394,7 +399,7 @@ class BatchedSolver:
     """
 
     def __init__(self, problems, *, tile="auto", order=0.0, converge="auto", method="ifim", max_iters=0,
-                 graph=True, schedule="persistent"):
+                 graph=True, schedule="persistent", remedy_order=0.0):
         F0 = problems[0][0]
         self.device, self.dtype = F0.device, F0.dtype
         if self.dtype not in _DT or not F0.is_cuda:
@@ -422,7 +427,8 @@ class BatchedSolver:
         # kernel or the asynchronous work queue), no host reads
         if schedule not in ("persistent", "async"):
             raise ValueError("a captured batch runs the persistent or the asynchronous schedule")
-        self._opt = _lib.make_options(tile, schedule, _DT[self.dtype], False, max_iters, order, converge, method)
+        self._opt = _lib.make_options(tile, schedule, _DT[self.dtype], False, max_iters, order, converge, method,
+                                      remedy_order=remedy_order)
         self._Foff, self._poff, self._soff = (_lib.i64_array(self.off), _lib.i64_array(self.off),
                                               _lib.i64_array(self.src_off))
         nbytes = self._lib.eik_workspace_size_batched(len(problems), self._grids, ctypes.byref(self._opt))

@@ -1,5 +1,5 @@
-"""Autotuner for the tile shape, the list order, the schedule and the Step-2
-convergence test of the solve.
+"""Autotuner for the tile shape, the list order (with the Step-3 bucket width),
+the schedule and the Step-2 convergence test of the solve.
 
 The best tile shape (4x4x4, 8x4x4, 8x8x4, 8x8x8; 16x16x1 or 8x8x1 in 2D),
 list order (bucketed or unordered), schedule (the persistent kernel with
@@ -35,9 +35,12 @@ from . import api
 # persistent schedule with either list order, and the asynchronous queue (which has no order); on
 # 8x8x8 tiles also the one-visit Step-2 test (measured on B300: 14 % faster on the 256^3
 # oscillating speed and 3 % on the 64-instance lognormal batch, 2x slower on the 16-shot tomography)
+# and Step-3 bucket widths 2 and 3 beside the default 4 (the batch was 6 % faster at width 2, the
+# 512^3 maze 13 % slower)
 CANDIDATES_3D = ([dict(tile=t, order=o, schedule="persistent") for t in ("8x8x4", "8x4x4", "4x4x4", "8x8x8")
                   for o in (0.0, -1.0)] + [dict(tile=t, order=-1.0, schedule="async") for t in ("8x8x4", "8x8x8")]
-                 + [dict(tile="8x8x8", order=0.0, schedule="persistent", converge="sweep")])
+                 + [dict(tile="8x8x8", order=0.0, schedule="persistent", converge=c, remedy_order=w)
+                    for c in ("auto", "sweep") for w in (0.0, 2.0, 3.0) if (c, w) != ("auto", 0.0)])
 CANDIDATES_2D = ([dict(tile=t, order=o, schedule="persistent") for t in ("16x16x1", "8x8x1") for o in (0.0, -1.0)]
                  + [dict(tile="16x16x1", order=-1.0, schedule="async")])
 
@@ -91,7 +94,8 @@ def _time_solve(problems, opts, reps):
 
 
 def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=None, force: bool = False) -> dict:
-    """Options (tile, order, schedule, converge) for this problem class, timed on `problems` on a cache miss.
+    """Options (tile, order, schedule, converge, remedy_order) for this problem class, timed on
+    `problems` on a cache miss.
 
     problems: a list of (F, src_idx, h) tuples (one for a single solve) on a CUDA
     device.  Returns a dict usable as keyword arguments of api.solve /
@@ -117,6 +121,8 @@ def tune(problems, *, cache_path: str | None = None, reps: int = 3, candidates=N
         name = f"{c['tile']}/order={c['order']}/{c.get('schedule', 'auto')}"
         if c.get("converge", "auto") != "auto":
             name += f"/converge={c['converge']}"
+        if c.get("remedy_order", 0.0):
+            name += f"/remedy_order={c['remedy_order']}"
         timings[name] = t
         if t < best_ms:
             best, best_ms = c, t

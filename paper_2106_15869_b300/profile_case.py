@@ -1,6 +1,7 @@
 """Run one named workload a fixed number of times, for a profiler to capture.
 
     python -m paper_2106_15869_b300.profile_case CASE [--calls N] [--stats] [--converge auto|confirm|sweep]
+                                                 [--remedy-order W]
 
 The cases are the benchmark workloads and smaller cases built by the same
 recipes (for captures that replay a kernel many times, which want a few GB on
@@ -60,17 +61,18 @@ def _tomo(dev, shots: int, adjoint: bool):
                                              return_stats=stats)
 
 
-def make_case(name: str, dev, converge: str = "auto"):
+def make_case(name: str, dev, converge: str = "auto", remedy_order: float = 0.0):
+    kw = dict(converge=converge, remedy_order=remedy_order)
     if name == "maze_512":
-        return _single(W.maze_3d(512), dev, converge=converge)
+        return _single(W.maze_3d(512), dev, **kw)
     if name == "maze_256":
-        return _single(W.maze_3d(256, n_slabs=8), dev, converge=converge)
+        return _single(W.maze_3d(256, n_slabs=8), dev, **kw)
     if name == "oscillating_256":
-        return _single(W.oscillating_3d(256), dev, converge=converge)
+        return _single(W.oscillating_3d(256), dev, **kw)
     if name == "batch64":
-        return _batch(W.lognormal_batch(64), dev, converge=converge)
+        return _batch(W.lognormal_batch(64), dev, **kw)
     if name == "batch16":
-        return _batch(W.lognormal_batch(64)[:16], dev, converge=converge)
+        return _batch(W.lognormal_batch(64)[:16], dev, **kw)
     if name == "tomo192_forward":
         return _tomo(dev, 16, False)
     if name == "tomo192_adjoint":
@@ -87,9 +89,11 @@ def main():
     ap.add_argument("--stats", action="store_true")
     ap.add_argument("--converge", default="auto", choices=["auto", "confirm", "sweep"],
                     help="Step-2 convergence test of the forward cases (the tomography keeps the default)")
+    ap.add_argument("--remedy-order", type=float, default=0.0,
+                    help="Step-3 list order of the forward cases (0 default, > 0 bucket width, < 0 unordered)")
     a = ap.parse_args()
     dev = torch.device("cuda", torch.cuda.current_device())
-    run = make_case(a.case, dev, a.converge)
+    run = make_case(a.case, dev, a.converge, a.remedy_order)
     for q in range(a.calls):
         out = run(a.stats)
         if a.stats:

@@ -40,9 +40,9 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_struct_sizes_match_header_layout():
-    # int64 x3 + double; int32,int32,int64,int32,int32,float,int32[3]; 7 int64 + 2 int32 + 2 double
+    # int64 x3 + double; int32,int32,int64,int32,int32,float,int32[3],float; 7 int64 + 2 int32 + 2 double
     assert ctypes.sizeof(_lib.eik_grid) == 48
-    assert ctypes.sizeof(_lib.eik_options) == 40
+    assert ctypes.sizeof(_lib.eik_options) == 48
     assert ctypes.sizeof(_lib.eik_stats) == 7 * 8 + 2 * 4 + 2 * 8
 
 
@@ -118,6 +118,10 @@ def test_host_argument_errors_before_device_work():
         assert lib.eik_solve(g, 1, None, None, 0, 1, 4096, 1 << 30, None, ctypes.byref(o3), None) == _lib.EIK_ERR_ARG
         assert lib.eik_workspace_size(g, ctypes.byref(o3)) == 0
     assert lib.eik_workspace_size(g, ctypes.byref(_lib.make_options(method="fim"))) > 0
+    # the Step-3 width: any number, not NaN
+    assert lib.eik_workspace_size(g, ctypes.byref(_lib.make_options(remedy_order=float("nan")))) == 0
+    for w in (-1.0, 2.0):
+        assert lib.eik_workspace_size(g, ctypes.byref(_lib.make_options(remedy_order=w))) > 0
     # batched: decreasing source offsets
     gb = _lib.grids_array([(8, 8, 8, 0.1), (8, 8, 8, 0.1)])
     rc = lib.eik_solve_batched(2, gb, 1, _lib.i64_array([0, 0]), 1, 1, _lib.i64_array([0, 3, 2]), 1,

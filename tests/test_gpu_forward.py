@@ -337,6 +337,22 @@ def test_converge_sweep_rule(schedule, order):
     assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
 
 
+@pytest.mark.parametrize("remedy_order", [2.0, 0.5, -1.0])
+@pytest.mark.parametrize("converge", ["auto", "sweep"])
+def test_remedy_order_widths(remedy_order, converge):
+    """The Step-3 list order alone (bucket widths and unordered), with either Step-2 test,
+    reaches the oracle's solution; on 2D grids (Step-2 lists bucketed) it is ignored."""
+    inst = W.maze_3d(64, seed=8, n_slabs=4, gap=10, n_src=3)
+    got, st = gpu_solve(inst, "fp32", remedy_order=remedy_order, converge=converge)
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+    assert st["tiles_flagged"] > 0
+    if remedy_order < 0:
+        assert st["tiles_deferred"] == 0                     # nothing waits in unordered lists
+    inst = W.paper_example_2d(5, 150)
+    got, _ = gpu_solve(inst, "fp32", remedy_order=remedy_order, converge=converge)
+    assert_parity(got, oracle_phi(inst, "fp32"), TOL32)
+
+
 def test_trace_records_iterations():
     torch = _torch()
     from paper_2106_15869_b300 import api
