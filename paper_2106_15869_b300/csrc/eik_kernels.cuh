@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
         bool thr = false;                              // this iteration in throughput mode
         if constexpr (MODE == kPersistLatency) {
             // more visits expected (the last iteration's, or the list) than groups: smaller
-            // groups, and the two-phase pass (classify the whole list, then one visit per grab)
+            // groups, one visit per grab (a bucketed list is classified first, in a phase of
+            // its own)
             if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (it > 0 ? s_p : n) > groups) {
                 if (!group_pass_split<T, BX, BY, BZ, false, kSmallGroupThreads>(
                         P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred, target))

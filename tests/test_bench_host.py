@@ -51,3 +51,11 @@ def test_captured_traffic_needs_the_captured_options(monkeypatch):
     assert bench.captured_traffic("tuned", opts={"tile": "8x8x8", "order": 0.0, "schedule": "persistent",
                                                  "converge": "sweep"}) == 2
     assert bench.captured_traffic("tuned", opts={"tile": "8x8x8", "order": 0.0}) is None
+
+
+def test_source_hash_ignores_comments_but_not_code():
+    a = "int f(int x) { return x + 1; }  // one\n/* two */"
+    b = "int  f(int x)\n{ return x + 1; }   // another comment"
+    c = "int f(int x) { return x + 2; }"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
