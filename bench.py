@@ -59,7 +59,7 @@ LAUNCHES_PER_SOLVE = 7
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the loop kernel
 # with the default options (or the ones an entry names), from one-pass ncu captures of that kernel
 # on the full workload (the ncu captures summarised with the profiles of this repository);
-# reported only for those options and while the kernel sources hash to the captured version
+# reported only for those options and while the kernel sources (comments stripped) hash to the captured version
 # (else null).
 MEASURED_TRAFFIC = {
     "maze_512": {"hash": "b62ee60ce7566606", "bytes": 3552605440 + 932409856},
