@@ -235,17 +235,6 @@ __device__ __forceinline__ int relax_tile(T *sm, T (&v)[TileGeom<BX, BY, BZ>::NP
     return mt.aniso ? sweep_loop(std::true_type{}) : sweep_loop(std::false_type{});
 }
 
-// faces (bit f) holding a node that dropped in this visit, over the warp
-template <int BX, int BY, int BZ>
-__device__ __forceinline__ int changed_faces(unsigned mine) {
-    using G = TileGeom<BX, BY, BZ>;
-    int f = 0;
-#pragma unroll
-    for (int m = 0; m < G::NPL; ++m)
-        if (mine >> m & 1) f |= G::faces_of(lane_id() + 32 * m);
-    return (int)__reduce_or_sync(kFull, (unsigned)f);
-}
-
 // Step-3 listing test.  A node p of a tile that dropped to value u can lower
 // the node q across face f of the neighbour tile only if u < phi(q): otherwise
 // the term ((phi - u)^+)^2 of q's eq. (6) stays 0 at phi(q), so q's root
