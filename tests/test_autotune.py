@@ -39,3 +39,24 @@ def test_tune_caches_and_solves(tmp_path):
     phi = api.solve(F, inst.src_idx, inst.h, **autotune.tuned_options([(F, inst.src_idx, inst.h)], cache_path=path))
     ref = oracle.fmm(inst.F.astype(np.float32).astype(np.float64), inst.h, inst.src_idx)
     assert np.max(np.abs(phi.cpu().double().numpy() - ref)) <= 1e-4 * ref.max()
+
+
+@pytest.mark.gpu
+def test_tune_2d_tries_the_step3_only_order(tmp_path):
+    import oracle
+    from paper_2106_15869_b300 import api
+    inst = W.paper_example_2d(3, 160)
+    F = torch.as_tensor(inst.F, dtype=torch.float32).cuda()
+    val = torch.as_tensor(inst.src_val, dtype=torch.float32).cuda()
+    path = str(tmp_path / "tune.json")
+    opts = autotune.tune([(F, inst.src_idx, inst.h)], cache_path=path, reps=1)
+    assert autotune.problem_key(F).startswith("d2")
+    assert any("remedy_order=4.0" in k for k in opts["_ms"])
+    kw = {k: v for k, v in opts.items() if not k.startswith("_")}
+    phi = api.solve(F, inst.src_idx, inst.h, val, **kw)
+    ref = oracle.fmm(inst.F.astype(np.float32).astype(np.float64), inst.h, inst.src_idx,
+                     inst.src_val.astype(np.float32).astype(np.float64))
+    fin = np.isfinite(ref)
+    got = phi.cpu().double().numpy()
+    assert np.array_equal(fin, np.isfinite(got))
+    assert np.max(np.abs(got[fin] - ref[fin])) <= 1e-4 * ref[fin].max()
