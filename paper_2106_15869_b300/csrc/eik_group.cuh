@@ -24,6 +24,11 @@ static_assert(kGroupThreads <= 32 * kWarpsPerCta, "a group fits in a CTA");
 // groups of the latency-only persistent kernel in iterations with more visits
 // expected than 256-thread groups: twice as many groups of half the size
 constexpr int kSmallGroupThreads = 128;
+// and in iterations with many more visits than that: groups of 64 threads, a
+// whole z column of an 8x8x8 tile per thread (a sweep is Gauss-Seidel along
+// the column), four times as many groups as 256-thread ones in flight
+constexpr int kColumnGroupThreads = 64;
+constexpr int kColumnGroupFactor = 4;     // expected visits above this many 256-thread groups
 
 template <int BX, int BY, int BZ, int MaxGT = kGroupThreads>
 struct GroupGeom {

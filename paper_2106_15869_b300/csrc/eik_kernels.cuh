@@ -378,10 +378,13 @@ template <class T, int BX, int BY, int BZ, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX, BY, BZ, MODE>()))
     k_persistent(FwdParams<T> P) {
     using GGS = GroupGeom<BX, BY, BZ, kSmallGroupThreads>;
-    constexpr int NGMAX = GGS::NG > GroupGeom<BX, BY, BZ>::NG ? GGS::NG : GroupGeom<BX, BY, BZ>::NG;
+    using GGC = GroupGeom<BX, BY, BZ, kColumnGroupThreads>;
+    constexpr int NG1 = GroupGeom<BX, BY, BZ>::NG;
+    constexpr int NGS = GGS::NG > NG1 ? GGS::NG : NG1;
+    constexpr int NGMAX = MODE == kPersistLatency && GGC::NG > NGS ? GGC::NG : NGS;
     __shared__ WarpSmem<T, BX, BY, BZ> sm;
     __shared__ GroupCtl gcs[NGMAX];
-    __shared__ GroupQueue gqs[NGMAX];
+    __shared__ GroupQueue gqs[NG1];                    // only the chunked passes of kGroupThreads groups queue
     __shared__ int s_n, s_p, s_visits;
     __shared__ unsigned s_k;
     T *my = sm.phi[warp_in_cta()];
@@ -425,7 +428,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, (persistent_min_ctas<T, BX,
             // more visits expected (the last iteration's, or the list) than groups: smaller
             // groups, one visit per grab (a bucketed list is classified first, in a phase of
             // its own)
-            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (it > 0 ? s_p : n) > groups) {
+            const int expv = it > 0 ? s_p : n;
+            if (GGC::NG > GGS::NG && expv > kColumnGroupFactor * groups) {
+                if (!group_pass_split<T, BX, BY, BZ, false, kColumnGroupThreads>(
+                        P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred, target))
+                    goto done;
+            } else if (GGS::NG > NG1 && expv > groups) {
                 if (!group_pass_split<T, BX, BY, BZ, false, kSmallGroupThreads>(
                         P, &sm.phi[0][0], gcs, it, n, kq, width, &s_visits, t_upd, sweeps, deferred, target))
                     goto done;
@@ -481,7 +489,12 @@ neighbour_check:
         }
         bool thr = false;
         if constexpr (MODE == kPersistLatency) {
-            if (GGS::NG > GroupGeom<BX, BY, BZ>::NG && (r > 0 ? s_p : n) > groups) {
+            const int expv = r > 0 ? s_p : n;
+            if (GGC::NG > GGS::NG && expv > kColumnGroupFactor * groups) {
+                if (!group_pass_split<T, BX, BY, BZ, true, kColumnGroupThreads>(
+                        P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t_rem, sweeps, deferred, target))
+                    goto done;
+            } else if (GGS::NG > NG1 && expv > groups) {
                 if (!group_pass_split<T, BX, BY, BZ, true, kSmallGroupThreads>(
                         P, &sm.phi[0][0], gcs, r, n, kq, width, &s_visits, t_rem, sweeps, deferred, target))
                     goto done;
