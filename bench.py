@@ -62,13 +62,13 @@ LAUNCHES_PER_SOLVE = 7
 # reported only for those options and while the kernel sources (comments stripped) hash to the captured version
 # (else null).
 MEASURED_TRAFFIC = {
-    "maze_512": {"hash": "6c969c13c8aa8289", "bytes": 3552605440 + 932409856},
-    "lognormal_batch64": {"hash": "6c969c13c8aa8289", "bytes": 9274621696 + 1568403200},
-    "lognormal_batch64_tuned": {"hash": "6c969c13c8aa8289", "bytes": 7099993856 + 1406834432,
+    "maze_512": {"hash": "35e2b5e8e7ed3dfa", "bytes": 3460604672 + 908771584},
+    "lognormal_batch64": {"hash": "35e2b5e8e7ed3dfa", "bytes": 9066408448 + 1564659456},
+    "lognormal_batch64_tuned": {"hash": "35e2b5e8e7ed3dfa", "bytes": 7149655552 + 1437020416,
                                 "opts": {"tile": "8x8x8", "order": 0.0, "schedule": "persistent",
                                          "converge": "sweep", "remedy_order": 2.0}},
-    "tomography_192_forward": {"hash": "6c969c13c8aa8289", "bytes": 2008364544 + 460832256},
-    "tomography_192_adjoint": {"hash": "ccdd37caf14d3d40", "bytes": 2792942336 + 412387072},
+    "tomography_192_forward": {"hash": "35e2b5e8e7ed3dfa", "bytes": 2011617024 + 463398912},
+    "tomography_192_adjoint": {"hash": "d42a46e339bf29bf", "bytes": 2806409216 + 413992704},
 }
 
 
