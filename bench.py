@@ -68,6 +68,7 @@ MEASURED_TRAFFIC = {
                                 "opts": {"tile": "8x8x8", "order": 0.0, "schedule": "persistent",
                                          "converge": "sweep", "remedy_order": 2.0}},
     "tomography_192_forward": {"hash": "35e2b5e8e7ed3dfa", "bytes": 2011617024 + 463398912},
+    "oscillating_256": {"hash": "35e2b5e8e7ed3dfa", "bytes": 349053696 + 82819072},
     "tomography_192_adjoint": {"hash": "d42a46e339bf29bf", "bytes": 2806409216 + 413992704},
 }
 
