@@ -35,12 +35,13 @@ from . import api
 # persistent schedule with either list order, and the asynchronous queue (which has no order); on
 # 8x8x8 tiles also the one-visit Step-2 test (measured on B300: 14 % faster on the 256^3
 # oscillating speed and 3 % on the 64-instance lognormal batch, 2x slower on the 16-shot tomography)
-# and Step-3 bucket widths 2 and 3 beside the default 4 (the batch was 6 % faster at width 2, the
-# 512^3 maze 13 % slower)
+# and Step-3 bucket widths beside the default 4 (measured on B300: the 64-instance batch is fastest
+# at width 2, the 512^3 maze at 5 to 6, 3 % faster than at 4, where the batch is 8 % slower)
 CANDIDATES_3D = ([dict(tile=t, order=o, schedule="persistent") for t in ("8x8x4", "8x4x4", "4x4x4", "8x8x8")
                   for o in (0.0, -1.0)] + [dict(tile=t, order=-1.0, schedule="async") for t in ("8x8x4", "8x8x8")]
                  + [dict(tile="8x8x8", order=0.0, schedule="persistent", converge=c, remedy_order=w)
-                    for c in ("auto", "sweep") for w in (0.0, 2.0, 3.0) if (c, w) != ("auto", 0.0)])
+                    for c in ("auto", "sweep") for w in (0.0, 2.0, 3.0) if (c, w) != ("auto", 0.0)]
+                 + [dict(tile="8x8x8", order=0.0, schedule="persistent", remedy_order=w) for w in (5.0, 6.0)])
 # 2D: also unordered Step-2 lists with bucketed Step-3 lists (measured at 4000^2: Example 3 9.7 ->
 # 5.7 ms and Example 1 6.4 -> 5.5 ms, Example 5 9.6 -> 15.4 ms against the 2D default, which buckets
 # both)
